@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark of the comb-spectrum hot path on GB300.
+
+Default workload: 10^6 frames x 1100 int16 samples at 1.1 GS/s (the paper's
+2.2 GB/s data rate, 1 MHz bins), 99 teeth at |51 + 10k| MHz, Lorentzian
+cavity (FWHM 80 MHz) driven at 23.686 kHz with 20 MHz amplitude, SNR 30 dB,
+12-bit samples; 2.2 GB resident on the device (larger than L2, so no flush is
+needed between steps).  One step = cg_process over all frames: cast, FFT,
+tooth readout, normalisation, moment initial guess and LM fit (20 iterations,
+tol 1e-6).  The metric is fitted spectra/s at fixed fit error (the sampled
+frames are checked against the FP64 oracle in the same run).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own 10^6 frames (weak scaling, no collective
+on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fitted spectra/s & input GB/s vs HBM peak at fixed fit error; p99 frame-to-fit"
+FWHM_HZ = 80e6
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_workload(n_frames, n_ref, device, seed_offset=0):
+    import synth
+    g = synth.PAPER_RATE
+    stream = synth.make_stream(g, synth.BASE_SEED + 2 + seed_offset)
+    fr = synth.frames(stream, n_frames, snr_db=30.0, center_amp_hz=20e6, device=device)
+    rf = synth.frames(stream, n_ref, cavity=False, snr_db=30.0, noise_stream=1, device=device)
+    return g, fr["frames"], rf["frames"]
+
+
+def cpu_baseline_leg(frames, params, status, iters, plan, ref, g, args) -> dict:
+    """CPU-baseline leg: the oracle, as it stands, timed on the host cores on a
+    bounded sample of the same frames; its outputs on a sample also give the
+    fit error of the GPU results (centres vs the oracle's converged optimum)."""
+    import oracle
+    frames_host = frames[: args.check_frames].cpu().numpy()
+    p_host = params[: args.check_frames].cpu().numpy()
+    bins, x = plan.bins, g.tooth_x
+    probe = min(512, frames_host.shape[0])
+    t = time.perf_counter()
+    oracle.process(frames_host[:probe], bins, ref, x)
+    dt = time.perf_counter() - t
+    n = int(min(frames_host.shape[0], max(probe, probe * args.cpu_seconds / max(dt, 1e-6))))
+    t = time.perf_counter()
+    oracle.process(frames_host[:n], bins, ref, x)
+    dt = time.perf_counter() - t
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cpu = {"value": n / dt, "unit": "spectra/s", "cores": cores, "kind": "oracle",
+           "sample": f"first {n} of the workload's frames (FP64 direct-sum DFT at the "
+                     f"99 teeth, moment init, 20-iteration LM), {dt:.1f} s"}
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(frames_host.shape[0], size=min(256, frames_host.shape[0]),
+                             replace=False))
+    o = oracle.process(frames_host[idx], bins, ref, x)
+    conv = oracle.fit_batch(o["y"], x, converged=True)
+    dc = np.abs(p_host[idx, 0] - conv["params"][:, 0])
+    st = status.cpu().numpy()
+    fe = {"frames_checked": int(idx.size), "center_err_max_hz": float(dc.max()),
+          "center_err_p99_hz": float(np.percentile(dc, 99)),
+          "frac_within_1e-4_fwhm": float(np.mean(dc <= 1e-4 * FWHM_HZ)),
+          "status_counts": {int(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
+          "mean_iters": float(iters.float().mean().item())}
+    return {"cpu_baseline": cpu, "fit_error": fe}
+
+
+def run_ours(args):
+    import torch
+    import paper_2307_12988_gb300 as cg
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.frames
+    g, frames, ref_frames = build_workload(n, args.ref_frames, dev, seed_offset=rank)
+    plan0 = cg.Plan(g.sample_rate, g.frame_len, g.tooth_freqs, g.tooth_x)
+    ref = plan0.reference_accumulate(ref_frames)
+    plan0.close()
+    del ref_frames
+    plan = cg.Plan(g.sample_rate, g.frame_len, g.tooth_freqs, g.tooth_x, ref,
+                   lanes_per_frame=args.lanes, fused=1 - args.unfused)
+    T = plan.T
+    amps = torch.empty((n, T), dtype=torch.float32, device=dev)
+    params = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    rss = torch.empty(n, dtype=torch.float32, device=dev)
+    iters = torch.empty(n, dtype=torch.int16, device=dev)
+    status = torch.empty(n, dtype=torch.int16, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        cg.cg_process(plan.handle, frames, n, amps, None, params, rss, iters, status, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+
+    hbm, _, peak_kind = _peaks()
+    bytes_per_frame = 2 * g.frame_len + 4 * T + 16 + 4 + 2 + 2
+    total_frames = n * ws
+    value = total_frames / (ms_step / 1e3)
+    achieved = bytes_per_frame * n / (ms_step / 1e3) / 1e9
+    result = {
+        "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded comb interferograms, 12-bit in int16)",
+        "config": {"workload": "paper_rate_1.1GSps_N1100_T99_1e6frames",
+                   "frames_per_gpu": n, "frame_len": g.frame_len, "teeth": T,
+                   "sample_rate_hz": g.sample_rate, "resident_bytes": 2 * g.frame_len * n,
+                   "l2": "inputs (2.2 GB) larger than L2; no flush",
+                   "lanes_per_frame": plan.info["lanes_per_frame"],
+                   "fused": plan.info["fused"], "fft_len": plan.info["fft_len"]},
+        "input_gbs": total_frames * 2 * g.frame_len / (ms_step / 1e3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_frame": bytes_per_frame},
+        "gpu_launches": args.steps * (1 if plan.info["fused"] else 2),
+        "clocks": clocks,
+    }
+    torch.cuda.synchronize()
+    if rank == 0 and not args.quick:
+        result.update(cpu_baseline_leg(frames, params, status, iters, plan, ref, g, args))
+    if not args.quick:
+        result["e2e"] = run_e2e(plan, frames, n, T, dev, args, ws)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    plan.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(plan, frames_dev, n, T, dev, args, ws):
+    """Same metric through cg_process with host buffers: every step copies the
+    frames from pinned host memory and reads every result back, in chunks on
+    two streams so copies overlap the kernel."""
+    import torch
+    import paper_2307_12988_gb300 as cg
+    N = plan.N
+    host_in = torch.empty((n, N), dtype=torch.int16, pin_memory=True)
+    host_in.copy_(frames_dev.cpu())
+    chunk = args.e2e_chunk
+    nch = (n + chunk - 1) // chunk
+    streams = [torch.cuda.Stream(dev) for _ in range(2)]
+    bufs = []
+    for _ in range(2):
+        bufs.append(dict(fr=torch.empty((chunk, N), dtype=torch.int16, device=dev),
+                         amps=torch.empty((chunk, T), dtype=torch.float32, device=dev),
+                         params=torch.empty((chunk, 4), dtype=torch.float32, device=dev),
+                         rss=torch.empty(chunk, dtype=torch.float32, device=dev),
+                         iters=torch.empty(chunk, dtype=torch.int16, device=dev),
+                         status=torch.empty(chunk, dtype=torch.int16, device=dev)))
+    host_out = dict(amps=torch.empty((n, T), dtype=torch.float32, pin_memory=True),
+                    params=torch.empty((n, 4), dtype=torch.float32, pin_memory=True),
+                    rss=torch.empty(n, dtype=torch.float32, pin_memory=True),
+                    iters=torch.empty(n, dtype=torch.int16, pin_memory=True),
+                    status=torch.empty(n, dtype=torch.int16, pin_memory=True))
+
+    def one_pass():
+        for c in range(nch):
+            s = streams[c % 2]
+            b = bufs[c % 2]
+            a0, a1 = c * chunk, min(n, (c + 1) * chunk)
+            m = a1 - a0
+            with torch.cuda.stream(s):
+                b["fr"][:m].copy_(host_in[a0:a1], non_blocking=True)
+                cg.cg_process(plan.handle, b["fr"], m, b["amps"], None, b["params"], b["rss"],
+                              b["iters"], b["status"], s)
+                for k in ("amps", "params", "rss", "iters", "status"):
+                    host_out[k][a0:a1].copy_(b[k][:m], non_blocking=True)
+
+    for _ in range(2):
+        one_pass()
+    torch.cuda.synchronize()
+    steps = max(1, args.e2e_steps)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one_pass()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    if ws > 1:
+        t = torch.tensor([dt], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dt = float(t.item())
+    d2h = n * (4 * T + 16 + 4 + 2 + 2)
+    return {"value": n * ws / dt, "unit": "spectra/s", "h2d_bytes_per_step": n * N * 2,
+            "d2h_bytes_per_step": d2h, "chunk_frames": chunk, "steps": steps,
+            "input_gbs": n * ws * N * 2 / dt / 1e9}
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores, on the same metric."""
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    g = synth.PAPER_RATE
+    stream = synth.make_stream(g, synth.BASE_SEED + 2)
+    n = args.ref_impl_frames
+    fr = synth.frames(stream, n, snr_db=30.0, center_amp_hz=20e6)["frames"]
+    rf = synth.frames(stream, 2000, cavity=False, snr_db=30.0, noise_stream=1)["frames"]
+    bins = oracle.tooth_bins(g.sample_rate, g.frame_len, g.tooth_freqs)
+    ref = oracle.reference(rf, bins)
+    for _ in range(args.warmup):
+        oracle.process(fr[: max(1, n // 8)], bins, ref, g.tooth_x)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.process(fr, bins, ref, g.tooth_x)
+        times.append(time.perf_counter() - t)
+    dt = sum(times) / len(times)
+    value = n / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "spectra/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "paper_rate_1.1GSps_N1100_T99_1e6frames",
+                      "sample_frames_per_step": n},
+           "cpu_baseline": {"value": value, "unit": "spectra/s", "cores": cores,
+                            "kind": "oracle",
+                            "sample": f"{n} frames of the workload per step"},
+           "e2e": {"value": value, "unit": "spectra/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=1_000_000)
+    ap.add_argument("--ref-frames", type=int, default=10_000)
+    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--unfused", type=int, default=0)
+    ap.add_argument("--quick", action="store_true", help="skip fit check, CPU baseline and e2e")
+    ap.add_argument("--check-frames", type=int, default=200_000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--e2e-chunk", type=int, default=65536)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--ref-impl-frames", type=int, default=20000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

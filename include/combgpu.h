@@ -1,0 +1,190 @@
+/*
+ * combgpu.h -- C ABI of the GB300 comb-spectrum readout and fitting library.
+ *
+ * The library turns digitised self-heterodyne comb interferograms into fitted
+ * cavity parameters, following arXiv 2307.12988 ("Data Capture and
+ * Processing"): integer samples are cast to floating point on the GPU, each
+ * frame is Fourier transformed, the comb-tooth bins are read out, divided by
+ * an averaged reference spectrum, and each normalised spectrum is fit by
+ * Levenberg-Marquardt.  The paper fits a Fano line with gpufit; this library
+ * fits the 4-parameter Lorentzian cavity mode
+ *     m(x) = B + A g^2 / ((x - c)^2 + g^2),   p = (c, g, A, B),
+ * g being the half width at half maximum, in the units of the tooth abscissa.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a cg_status; no exception or signal crosses the ABI.
+ *     cg_last_error() gives a thread-local description of the last failure.
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *     library never frees or retains them after the call returns.  Pointers
+ *     named *_host are host memory, read or written before the call returns
+ *     unless stated otherwise.
+ *   - Work is enqueued asynchronously on the caller's CUDA stream
+ *     (`cuda_stream`, a cudaStream_t; NULL = the legacy default stream).
+ *   - A plan belongs to the device that was current when it was made; use it
+ *     from one host thread at a time.
+ *   - Arrays are row-major: frames [n][N] int16, per-tooth outputs [n][T],
+ *     parameters [n][4] in the order (c, g, A, B).
+ */
+#ifndef COMBGPU_H
+#define COMBGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CG_VERSION 100
+
+typedef enum cg_status {
+    CG_OK = 0,
+    CG_ERR_ARG = 1,           /* invalid argument (NULL, size, alignment) */
+    CG_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    CG_ERR_NOMEM = 3,         /* device or host allocation failed */
+    CG_ERR_TOOTH_RANGE = 4,   /* a tooth lies outside [0, fs/2] after aliasing rules */
+    CG_ERR_OVERFLOW = 5,      /* streaming ring overflowed (frames dropped) */
+    CG_ERR_TIMEOUT = 6,       /* a bounded wait ran out */
+    CG_ERR_DEVICE_CHECK = 7,  /* a kernel's own check failed */
+    CG_ERR_UNSUPPORTED = 8,   /* geometry or option not supported */
+    CG_ERR_STATE = 9          /* call not valid in the object's current state */
+} cg_status;
+
+/* Per-frame fit outcome, written to status_dev (int16). */
+#define CG_FIT_CONVERGED 0    /* a trial step changed chi^2 by <= tol * chi^2 */
+#define CG_FIT_MAX_ITER 1     /* max_iter trial steps without convergence */
+#define CG_FIT_SINGULAR 2     /* J^T J not positive definite */
+#define CG_FIT_NONFINITE 3    /* the spectrum or chi^2 at the start is not finite */
+#define CG_FIT_INIT_FLAT 0x10 /* flag: moment initial guess saw a flat spectrum */
+
+enum { CG_READOUT_FFT = 0, CG_READOUT_GEMM_SPLIT = 1 };
+enum { CG_FFT_AUTO = 0, CG_FFT_FULL = 1, CG_FFT_COSET = 2 };
+enum { CG_INIT_MOMENT = 0, CG_INIT_MLP = 1 };
+
+/* Options of a plan.  Fill with cg_opts_default() and change what you need. */
+typedef struct cg_opts {
+    int readout;          /* CG_READOUT_FFT (default) */
+    int fft;              /* CG_FFT_AUTO: coset-pruned transform when every tooth bin
+                             lies in one residue pair +-r mod M (M | N), else full */
+    int init;             /* CG_INIT_MOMENT (default) */
+    int max_iter;         /* LM trial steps per frame; paper: 20 */
+    double tol;           /* relative chi^2 change for convergence; paper: 1e-6 */
+    double lambda0;       /* initial Marquardt damping; 1e-3 */
+    int lanes_per_frame;  /* LM lanes cooperating on one frame: 4, 8, 16 or 32
+                             (32 = one warp per frame); 0 = library default */
+    int fused;            /* 1 (default): readout and fit in one kernel;
+                             0: a readout kernel then a fit kernel */
+    int reserved[8];      /* must be zero */
+} cg_opts;
+
+typedef struct cg_plan_s* cg_plan_t;
+
+/* Summary of what a plan decided (for logging and tests). */
+typedef struct cg_plan_info {
+    int frame_len;        /* N */
+    int n_teeth;          /* T */
+    int fft_kind;         /* CG_FFT_FULL or CG_FFT_COSET */
+    int coset_modulus;    /* M (coset transform) or 2 (full real transform) */
+    int coset_residue;    /* r (coset transform) */
+    int fft_len;          /* complex transform length L = N / M */
+    int n_radices;        /* number of shared-memory FFT stages */
+    int radices[8];
+    int frames_per_cta;   /* frames one thread block transforms at a time */
+    int lanes_per_frame;  /* LM lanes per frame */
+    int n_collisions;     /* pairs of teeth that read the same bin */
+    int fused;
+} cg_plan_info;
+
+/* Fill *opts with the defaults (FFT readout, moment init, 20 iterations,
+ * tol 1e-6, lambda0 1e-3, fused kernel).  opts must not be NULL. */
+void cg_opts_default(cg_opts* opts);
+
+/*
+ * cg_plan -- precompute everything that depends on the instrument geometry
+ * (paper, "Data Capture and Processing": frames of N samples, tooth bins
+ * "selected and mapped" into the optical spectrum, a pre-calculated average
+ * reference spectrum).
+ *   sample_rate   digitiser rate fs in Hz (> 0)
+ *   frame_len     N samples per frame, 8 <= N <= 16384
+ *   n_teeth       T teeth read out, 5 <= T <= 1024
+ *   tooth_freqs   host [T]: signed RF frequency of each tooth in Hz; its bin is
+ *                 floor(|f| N / fs + 1/2) reduced mod N and folded into [0, N/2]
+ *   tooth_x       host [T] or NULL: fit abscissa of each tooth (e.g. optical
+ *                 offset in Hz); NULL uses tooth_freqs
+ *   ref_spectrum  host [T] or NULL: mean |X| of cavity-free frames per tooth
+ *                 (must be > 0); NULL means 1 (y equals the raw magnitudes)
+ *   opts          NULL for defaults
+ * All host arrays are copied.  On success *plan owns device memory until
+ * cg_plan_destroy.  Errors: CG_ERR_ARG, CG_ERR_UNSUPPORTED (N not a product of
+ * radices 2,3,5,7,11,13), CG_ERR_NOMEM, CG_ERR_CUDA.
+ */
+cg_status cg_plan(cg_plan_t* plan, double sample_rate, int frame_len, int n_teeth,
+                  const double* tooth_freqs, const double* tooth_x,
+                  const double* ref_spectrum, const cg_opts* opts);
+
+/* Release a plan (NULL is ignored).  Synchronises the plan's device first. */
+void cg_plan_destroy(cg_plan_t plan);
+
+/* Describe a plan; bins_host (may be NULL) receives the T folded bins. */
+cg_status cg_plan_describe(cg_plan_t plan, cg_plan_info* info, int* bins_host);
+
+/* Replace the reference spectrum (host [T], every value > 0). */
+cg_status cg_set_reference(cg_plan_t plan, const double* ref_spectrum);
+
+/*
+ * cg_process -- the whole per-frame path on n_frames frames resident on the
+ * device: cast, transform, tooth readout, normalisation, initial guess and
+ * LM fit (paper, "Data Capture and Processing", both paragraphs on the fit).
+ *   frames_dev   int16 [n_frames][N], 2-byte aligned (16-byte alignment is
+ *                faster); samples are read as signed integers
+ *   amps_dev     float [n_frames][T]: |X_b| at each tooth (required)
+ *   y_dev        float [n_frames][T] or NULL: amps / reference
+ *   params_dev   float [n_frames][4]: (c, g, A, B), g >= 0, abscissa units
+ *   rss_dev      float [n_frames] or NULL: sum of squared residuals of y
+ *   iters_dev    int16 [n_frames] or NULL: LM trial steps taken
+ *   status_dev   int16 [n_frames] or NULL: CG_FIT_* outcome | flags
+ * n_frames == 0 is a no-op.  Asynchronous on cuda_stream.
+ */
+cg_status cg_process(cg_plan_t plan, const int16_t* frames_dev, int64_t n_frames,
+                     float* amps_dev, float* y_dev, float* params_dev, float* rss_dev,
+                     int16_t* iters_dev, int16_t* status_dev, void* cuda_stream);
+
+/*
+ * cg_readout -- only the cast, transform and tooth readout (with
+ * normalisation when y_dev is not NULL) of cg_process.
+ */
+cg_status cg_readout(cg_plan_t plan, const int16_t* frames_dev, int64_t n_frames,
+                     float* amps_dev, float* y_dev, void* cuda_stream);
+
+/*
+ * cg_fit -- only the initial guess and LM fit of cg_process, on normalised
+ * spectra y_dev float [n][T].  p0_dev float [n][4] (abscissa units) or NULL
+ * for the moment initial guess.  Outputs as in cg_process.
+ */
+cg_status cg_fit(cg_plan_t plan, const float* y_dev, int64_t n, const float* p0_dev,
+                 float* params_dev, float* rss_dev, int16_t* iters_dev,
+                 int16_t* status_dev, void* cuda_stream);
+
+/*
+ * cg_reference_accumulate -- averaged reference spectrum (paper: "a
+ * pre-calculated average reference spectrum, typically recorded at the
+ * beginning of the experiment"): ref_host[k] = mean over the n cavity-free
+ * frames of |X_{b_k}|, accumulated in FP64 on the device.  Blocks until the
+ * result is in ref_host (double [T]).  Does not change the plan's reference.
+ */
+cg_status cg_reference_accumulate(cg_plan_t plan, const int16_t* frames_dev, int64_t n,
+                                  double* ref_host, void* cuda_stream);
+
+/* Text of a status code (static storage). */
+const char* cg_status_string(cg_status status);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* cg_last_error(void);
+
+/* CG_VERSION of the loaded library. */
+int cg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COMBGPU_H */

@@ -1,0 +1,216 @@
+"""ctypes binding of libcombgpu.so: argument marshalling only.
+
+Every function here has the name of the C entry point it calls (see
+include/combgpu.h) and does no arithmetic of the method: device buffers are
+passed as raw pointers (a torch CUDA tensor or an integer address), host
+arrays as numpy arrays.  Loading fails loudly when the CUDA library is not
+built; there is no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+CG_OK = 0
+STATUS_NAMES = {0: "CG_OK", 1: "CG_ERR_ARG", 2: "CG_ERR_CUDA", 3: "CG_ERR_NOMEM",
+                4: "CG_ERR_TOOTH_RANGE", 5: "CG_ERR_OVERFLOW", 6: "CG_ERR_TIMEOUT",
+                7: "CG_ERR_DEVICE_CHECK", 8: "CG_ERR_UNSUPPORTED", 9: "CG_ERR_STATE"}
+FIT_CONVERGED, FIT_MAX_ITER, FIT_SINGULAR, FIT_NONFINITE, FIT_INIT_FLAT = 0, 1, 2, 3, 0x10
+READOUT_FFT, READOUT_GEMM_SPLIT = 0, 1
+FFT_AUTO, FFT_FULL, FFT_COSET = 0, 1, 2
+INIT_MOMENT, INIT_MLP = 0, 1
+
+
+class CgError(RuntimeError):
+    """A library call returned a status other than CG_OK."""
+
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {detail}")
+
+
+class cg_opts(ctypes.Structure):
+    _fields_ = [("readout", ctypes.c_int), ("fft", ctypes.c_int), ("init", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
+                ("lambda0", ctypes.c_double), ("lanes_per_frame", ctypes.c_int),
+                ("fused", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+
+
+class cg_plan_info(ctypes.Structure):
+    _fields_ = [("frame_len", ctypes.c_int), ("n_teeth", ctypes.c_int),
+                ("fft_kind", ctypes.c_int), ("coset_modulus", ctypes.c_int),
+                ("coset_residue", ctypes.c_int), ("fft_len", ctypes.c_int),
+                ("n_radices", ctypes.c_int), ("radices", ctypes.c_int * 8),
+                ("frames_per_cta", ctypes.c_int), ("lanes_per_frame", ctypes.c_int),
+                ("n_collisions", ctypes.c_int), ("fused", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "cg_opts_default": (None, [ctypes.POINTER(cg_opts)]),
+    "cg_plan": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                               _P, _P, _P, ctypes.POINTER(cg_opts)]),
+    "cg_plan_destroy": (None, [_P]),
+    "cg_plan_describe": (ctypes.c_int, [_P, ctypes.POINTER(cg_plan_info), _P]),
+    "cg_set_reference": (ctypes.c_int, [_P, _P]),
+    "cg_process": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P]),
+    "cg_readout": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
+    "cg_fit": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
+    "cg_reference_accumulate": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    "cg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "cg_last_error": (ctypes.c_char_p, []),
+    "cg_version": (ctypes.c_int, []),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcombgpu.so (building it first when it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libcombgpu.so is not built ({_build.LIB}); run "
+                              "paper_2307_12988_gb300.build.build() with nvcc available")
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _ptr(x) -> int | None:
+    """Device or host address of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:   # torch absent: legacy default stream
+            return None
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(st: int, where: str):
+    if st != CG_OK:
+        detail = load().cg_last_error().decode(errors="replace")
+        raise CgError(st, where, detail)
+
+
+def cg_opts_default(**overrides) -> cg_opts:
+    o = cg_opts()
+    load().cg_opts_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def cg_plan(sample_rate: float, frame_len: int, tooth_freqs, tooth_x=None, ref_spectrum=None,
+            opts: cg_opts | None = None) -> int:
+    f = np.ascontiguousarray(tooth_freqs, dtype=np.float64)
+    x = None if tooth_x is None else np.ascontiguousarray(tooth_x, dtype=np.float64)
+    r = None if ref_spectrum is None else np.ascontiguousarray(ref_spectrum, dtype=np.float64)
+    if x is not None and x.size != f.size or r is not None and r.size != f.size:
+        raise ValueError("tooth_x / ref_spectrum must have one value per tooth")
+    h = _P()
+    st = load().cg_plan(ctypes.byref(h), float(sample_rate), int(frame_len), int(f.size),
+                        _ptr(f), _ptr(x), _ptr(r), ctypes.byref(opts) if opts else None)
+    _check(st, "cg_plan")
+    return h.value
+
+
+def cg_plan_destroy(plan: int) -> None:
+    if plan:
+        load().cg_plan_destroy(plan)
+
+
+def cg_plan_describe(plan: int) -> dict:
+    info = cg_plan_info()
+    probe = cg_plan_info()
+    _check(load().cg_plan_describe(plan, ctypes.byref(probe), None), "cg_plan_describe")
+    bins = np.empty(probe.n_teeth, dtype=np.int32)
+    _check(load().cg_plan_describe(plan, ctypes.byref(info), _ptr(bins)), "cg_plan_describe")
+    d = {name: getattr(info, name) for name, _ in cg_plan_info._fields_}
+    d["radices"] = list(info.radices)[:info.n_radices]
+    d["bins"] = bins
+    return d
+
+
+def cg_set_reference(plan: int, ref_spectrum) -> None:
+    r = np.ascontiguousarray(ref_spectrum, dtype=np.float64)
+    _check(load().cg_set_reference(plan, _ptr(r)), "cg_set_reference")
+
+
+def cg_process(plan: int, frames, n_frames: int, amps, y, params, rss, iters, status,
+               stream=None) -> None:
+    _check(load().cg_process(plan, _ptr(frames), int(n_frames), _ptr(amps), _ptr(y),
+                             _ptr(params), _ptr(rss), _ptr(iters), _ptr(status),
+                             _stream(stream)), "cg_process")
+
+
+def cg_readout(plan: int, frames, n_frames: int, amps, y, stream=None) -> None:
+    _check(load().cg_readout(plan, _ptr(frames), int(n_frames), _ptr(amps), _ptr(y),
+                             _stream(stream)), "cg_readout")
+
+
+def cg_fit(plan: int, y, n: int, p0, params, rss, iters, status, stream=None) -> None:
+    _check(load().cg_fit(plan, _ptr(y), int(n), _ptr(p0), _ptr(params), _ptr(rss),
+                         _ptr(iters), _ptr(status), _stream(stream)), "cg_fit")
+
+
+def cg_reference_accumulate(plan: int, frames, n: int, stream=None) -> np.ndarray:
+    ref = None
+    info = cg_plan_describe(plan)
+    ref = np.empty(info["n_teeth"], dtype=np.float64)
+    _check(load().cg_reference_accumulate(plan, _ptr(frames), int(n), _ptr(ref),
+                                          _stream(stream)), "cg_reference_accumulate")
+    return ref
+
+
+def cg_status_string(status: int) -> str:
+    return load().cg_status_string(int(status)).decode()
+
+
+def cg_last_error() -> str:
+    return load().cg_last_error().decode(errors="replace")
+
+
+def cg_version() -> int:
+    return load().cg_version()

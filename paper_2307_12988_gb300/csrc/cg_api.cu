@@ -1,0 +1,475 @@
+// cg_api.cu -- the C ABI: plan construction and the plain-path entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "cg_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+cg_status fail(cg_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+cg_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? CG_ERR_NOMEM : CG_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+constexpr double kTwoPi = 6.28318530717958647692528676655900577;
+
+// radices of the shared-memory stages, largest first among powers of two
+bool factorize(int L, std::vector<int>& out)
+{
+    out.clear();
+    int r = L;
+    while (r % 8 == 0 && r > 8) { out.push_back(8); r /= 8; }
+    if (r == 8) { out.push_back(8); r = 1; }
+    while (r % 4 == 0) { out.push_back(4); r /= 4; }
+    while (r % 2 == 0) { out.push_back(2); r /= 2; }
+    for (int q : {5, 3, 7, 11, 13})
+        while (r % q == 0) { out.push_back(q); r /= q; }
+    return r == 1 && static_cast<int>(out.size()) <= cg::kMaxStages;
+}
+
+// Choose the transform: the largest M | N (4 <= M, N/M >= 2) such that every
+// tooth bin is congruent to +r or -r mod M, so the teeth are read from one
+// L = N/M point transform of the folded frame; otherwise the real FFT through
+// an N/2-point complex transform (N even) or the complex N-point one (M = 1).
+void choose_fft(cg_plan_s* p)
+{
+    const int N = p->N;
+    p->kind = CG_FFT_FULL;
+    p->M = 2;
+    p->r0 = 0;
+    p->L = N / 2;
+    std::vector<int> rad;
+    if (p->opts.fft != CG_FFT_FULL) {
+        for (int M = N / 2; M >= 4; --M) {
+            if (N % M) continue;
+            const int L = N / M;
+            if (L < 2 || M > 4096) continue;
+            const int r = p->bins[0] % M;
+            bool ok = true;
+            for (int b : p->bins) {
+                const int q = b % M;
+                if (q != r && q != (M - r) % M) { ok = false; break; }
+            }
+            if (!ok || !factorize(L, rad)) continue;
+            p->kind = CG_FFT_COSET;
+            p->M = M;
+            p->r0 = r;
+            p->L = L;
+            p->radices = rad;
+            return;
+        }
+    }
+    if (N % 2 == 0 && factorize(N / 2, rad)) {
+        p->radices = rad;
+        return;
+    }
+    // odd N: complex transform of the real samples (a fold with M = 1)
+    p->kind = CG_FFT_COSET;
+    p->M = 1;
+    p->r0 = 0;
+    p->L = N;
+    if (!factorize(N, rad)) p->radices.clear();
+    else p->radices = rad;
+}
+
+int align16(int v) { return (v + 15) & ~15; }
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& src)
+{
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), sizeof(T) * std::max<size_t>(src.size(), 1));
+    if (e != cudaSuccess) return e;
+    if (!src.empty()) e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+void free_tables(cg::DevTables& d)
+{
+    cudaFree(d.tw_L);
+    cudaFree(d.tw_M);
+    cudaFree(d.tw_n1);
+    cudaFree(d.tw_b);
+    cudaFree(d.zidx);
+    cudaFree(d.inv_ref);
+    cudaFree(d.u);
+    cudaFree(d.outer_idx);
+    cudaFree(d.ref_part);
+    cudaFree(d.ref_out);
+    d = cg::DevTables{};
+}
+
+std::vector<float> inv_ref_of(const std::vector<double>& ref)
+{
+    std::vector<float> v(ref.size());
+    for (size_t i = 0; i < ref.size(); ++i) v[i] = static_cast<float>(1.0 / ref[i]);
+    return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cg_opts_default(cg_opts* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->readout = CG_READOUT_FFT;
+    o->fft = CG_FFT_AUTO;
+    o->init = CG_INIT_MOMENT;
+    o->max_iter = 20;
+    o->tol = 1e-6;
+    o->lambda0 = 1e-3;
+    o->lanes_per_frame = 0;
+    o->fused = 1;
+}
+
+const char* cg_status_string(cg_status s)
+{
+    switch (s) {
+    case CG_OK: return "ok";
+    case CG_ERR_ARG: return "invalid argument";
+    case CG_ERR_CUDA: return "CUDA error";
+    case CG_ERR_NOMEM: return "out of memory";
+    case CG_ERR_TOOTH_RANGE: return "tooth out of range";
+    case CG_ERR_OVERFLOW: return "ring buffer overflow";
+    case CG_ERR_TIMEOUT: return "timeout";
+    case CG_ERR_DEVICE_CHECK: return "device-side check failed";
+    case CG_ERR_UNSUPPORTED: return "unsupported";
+    case CG_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char* cg_last_error(void) { return g_last_error.c_str(); }
+
+int cg_version(void) { return CG_VERSION; }
+
+cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_freqs,
+                  const double* tooth_x, const double* ref, const cg_opts* opts)
+{
+    g_last_error.clear();
+    if (!out) return fail(CG_ERR_ARG, "plan pointer is NULL");
+    *out = nullptr;
+    if (!(fs > 0.0) || !std::isfinite(fs)) return fail(CG_ERR_ARG, "sample_rate must be > 0");
+    if (N < cg::kMinN || N > cg::kMaxN) return fail(CG_ERR_ARG, "frame_len %d outside [%d, %d]", N, cg::kMinN, cg::kMaxN);
+    if (T < cg::kMinT || T > cg::kMaxT) return fail(CG_ERR_ARG, "n_teeth %d outside [%d, %d]", T, cg::kMinT, cg::kMaxT);
+    if (!tooth_freqs) return fail(CG_ERR_ARG, "tooth_freqs is NULL");
+    cg_opts o;
+    cg_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.max_iter < 0 || o.max_iter > 32767) return fail(CG_ERR_ARG, "max_iter outside [0, 32767]");
+    if (!(o.tol >= 0.0) || !(o.lambda0 > 0.0)) return fail(CG_ERR_ARG, "tol must be >= 0 and lambda0 > 0");
+    if (o.lanes_per_frame != 0 && o.lanes_per_frame != 4 && o.lanes_per_frame != 8 &&
+        o.lanes_per_frame != 16 && o.lanes_per_frame != 32)
+        return fail(CG_ERR_ARG, "lanes_per_frame must be 0, 4, 8, 16 or 32");
+    if (o.readout != CG_READOUT_FFT) return fail(CG_ERR_UNSUPPORTED, "readout kind %d not available", o.readout);
+    if (o.init != CG_INIT_MOMENT) return fail(CG_ERR_UNSUPPORTED, "init kind %d not available", o.init);
+    for (int i = 0; i < 8; ++i)
+        if (o.reserved[i] != 0) return fail(CG_ERR_ARG, "reserved option fields must be zero");
+
+    auto* p = new cg_plan_s();
+    p->fs = fs;
+    p->N = N;
+    p->T = T;
+    p->opts = o;
+    p->bins.resize(T);
+    p->x.resize(T);
+    p->ref.assign(T, 1.0);
+    for (int k = 0; k < T; ++k) {
+        const double f = tooth_freqs[k];
+        if (!std::isfinite(f)) { delete p; return fail(CG_ERR_ARG, "tooth_freqs[%d] is not finite", k); }
+        const double pos = std::fabs(f) * static_cast<double>(N) / fs;
+        if (pos > 1e15) { delete p; return fail(CG_ERR_TOOTH_RANGE, "tooth %d far beyond the sample rate", k); }
+        long long b = static_cast<long long>(std::floor(pos + 0.5)) % N;
+        if (b > N / 2) b = N - b;
+        p->bins[k] = static_cast<int>(b);
+        p->x[k] = tooth_x ? tooth_x[k] : f;
+        if (!std::isfinite(p->x[k])) { delete p; return fail(CG_ERR_ARG, "tooth_x[%d] is not finite", k); }
+        if (ref) {
+            if (!(ref[k] > 0.0) || !std::isfinite(ref[k])) { delete p; return fail(CG_ERR_ARG, "ref_spectrum[%d] must be > 0", k); }
+            p->ref[k] = ref[k];
+        }
+    }
+    for (int i = 0; i < T; ++i)
+        for (int j = i + 1; j < T; ++j)
+            if (p->bins[i] == p->bins[j]) ++p->n_collisions;
+
+    // abscissa normalisation u = (x - x_mid) / x_scale, x_scale = mean spacing
+    const double xmin = *std::min_element(p->x.begin(), p->x.end());
+    const double xmax = *std::max_element(p->x.begin(), p->x.end());
+    if (!(xmax > xmin)) { delete p; return fail(CG_ERR_ARG, "tooth_x values must not all be equal"); }
+    p->x_mid = 0.5 * (xmin + xmax);
+    p->x_scale = (xmax - xmin) / static_cast<double>(T - 1);
+    std::vector<float> u(T);
+    for (int k = 0; k < T; ++k) u[k] = static_cast<float>((p->x[k] - p->x_mid) / p->x_scale);
+    p->u_mid = 0.0f;
+    p->du = 1.0f;
+    p->span = static_cast<float>(T - 1);
+    // outer fifth of the teeth by distance from the span midpoint (ties kept)
+    {
+        std::vector<double> dist(T);
+        for (int k = 0; k < T; ++k) dist[k] = std::fabs(p->x[k] - p->x_mid);
+        std::vector<double> s = dist;
+        std::sort(s.begin(), s.end());
+        const int no = (T + 4) / 5;
+        const double thr = s[T - no];
+        std::vector<int> idx;
+        for (int k = 0; k < T; ++k)
+            if (dist[k] >= thr) idx.push_back(k);
+        p->n_outer = static_cast<int>(idx.size());
+        cudaError_t e = cudaGetDevice(&p->device);
+        if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaGetDevice"); }
+        e = upload(&p->d.outer_idx, idx);
+        if (e != cudaSuccess) { free_tables(p->d); delete p; return cuda_fail(e, "outer index upload"); }
+    }
+    cudaError_t e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) { free_tables(p->d); delete p; return cuda_fail(e, "SM count"); }
+
+    choose_fft(p);
+    if (p->radices.empty()) {
+        free_tables(p->d);
+        delete p;
+        return fail(CG_ERR_UNSUPPORTED, "frame_len %d: transform length is not a product of 2,3,5,7,11,13", N);
+    }
+    p->G = o.lanes_per_frame ? o.lanes_per_frame : 8;
+
+    // twiddles (FP64 on the host, rounded to FP32)
+    const int L = p->L, M = p->M;
+    std::vector<float2> twL(L), twM(std::max(M, 1)), twn1(L), twb(T);
+    for (int m = 0; m < L; ++m) {
+        const double a = -kTwoPi * static_cast<double>(m) / L;
+        twL[m] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+    }
+    std::vector<int> zidx(T);
+    if (p->kind == CG_FFT_COSET) {
+        for (int n2 = 0; n2 < M; ++n2) {
+            const double a = -kTwoPi * static_cast<double>((static_cast<long long>(p->r0) * n2) % M) / M;
+            twM[n2] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+        }
+        for (int n1 = 0; n1 < L; ++n1) {
+            const double a = -kTwoPi * static_cast<double>((static_cast<long long>(p->r0) * n1) % N) / N;
+            twn1[n1] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+        }
+        for (int k = 0; k < T; ++k) {
+            const int b = p->bins[k];
+            int m;
+            if (((b - p->r0) % M + M) % M == 0) m = (b - p->r0) / M;
+            else m = (N - b - p->r0) / M;   // conjugate-symmetric partner N - b
+            zidx[k] = ((m % L) + L) % L;
+        }
+    } else {
+        for (int k = 0; k < T; ++k) {
+            const int b = p->bins[k];
+            const double a = -kTwoPi * static_cast<double>(b) / N;
+            twb[k] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+            zidx[k] = b;
+        }
+    }
+
+    // batch size and shared-memory layout
+    cg::ReadoutArgs& ra = p->ra;
+    ra.N = N;
+    ra.T = T;
+    ra.L = L;
+    ra.M = M;
+    ra.r0 = p->r0;
+    ra.kind = p->kind;
+    ra.nst = static_cast<int>(p->radices.size());
+    for (int s = 0; s < cg::kMaxStages; ++s) ra.radix[s] = s < ra.nst ? p->radices[s] : 1;
+    ra.fstride = L;
+    ra.ystride = T;
+    int tables = 0;
+    ra.sm_twL = tables; tables = align16(tables + 8 * L);
+    ra.sm_twM = tables; tables = align16(tables + 8 * std::max(M, 1));
+    ra.sm_twn1 = tables; tables = align16(tables + 8 * L);
+    ra.sm_twb = tables; tables = align16(tables + 8 * T);
+    ra.sm_zidx = tables; tables = align16(tables + 4 * T);
+    ra.sm_iref = tables; tables = align16(tables + 4 * T);
+    ra.sm_u = tables; tables = align16(tables + 4 * T);
+    ra.sm_acc = tables; tables = align16(tables + 8 * T);
+    const int per_frame = 2 * N + 2 * 8 * ra.fstride + 4 * ra.ystride;
+    const int budget = 100 * 1024;
+    int F = (budget - tables) / per_frame;
+    F = std::max(1, std::min(F, 64));
+    ra.F = F;
+    p->F = F;
+    ra.sm_raw = tables;
+    int off = align16(tables + 2 * N * F + 32);
+    ra.sm_a = off; off = align16(off + 8 * ra.fstride * F);
+    ra.sm_b = off; off = align16(off + 8 * ra.fstride * F);
+    ra.sm_y = off; off = align16(off + 4 * ra.ystride * F);
+    ra.sm_total = off;
+    if (ra.sm_total > 227 * 1024) {
+        free_tables(p->d);
+        delete p;
+        return fail(CG_ERR_UNSUPPORTED, "frame_len %d needs %d bytes of shared memory", N, ra.sm_total);
+    }
+
+    std::vector<float> iref = inv_ref_of(p->ref);
+    if ((e = upload(&p->d.tw_L, twL)) != cudaSuccess || (e = upload(&p->d.tw_M, twM)) != cudaSuccess ||
+        (e = upload(&p->d.tw_n1, twn1)) != cudaSuccess || (e = upload(&p->d.tw_b, twb)) != cudaSuccess ||
+        (e = upload(&p->d.zidx, zidx)) != cudaSuccess || (e = upload(&p->d.inv_ref, iref)) != cudaSuccess ||
+        (e = upload(&p->d.u, u)) != cudaSuccess) {
+        free_tables(p->d);
+        delete p;
+        return cuda_fail(e, "table upload");
+    }
+    ra.tw_L = p->d.tw_L;
+    ra.tw_M = p->d.tw_M;
+    ra.tw_n1 = p->d.tw_n1;
+    ra.tw_b = p->d.tw_b;
+    ra.zidx = p->d.zidx;
+    ra.inv_ref = p->d.inv_ref;
+    ra.u = p->d.u;
+
+    if ((e = cg::configure_kernels(p)) != cudaSuccess) {
+        free_tables(p->d);
+        delete p;
+        return cuda_fail(e, "kernel configuration");
+    }
+    p->d.ref_part_rows = p->grid_readout;
+    if ((e = cudaMalloc(&p->d.ref_part, sizeof(double) * static_cast<size_t>(p->d.ref_part_rows) * T)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d.ref_out, sizeof(double) * T)) != cudaSuccess) {
+        free_tables(p->d);
+        delete p;
+        return cuda_fail(e, "reference scratch");
+    }
+    *out = p;
+    return CG_OK;
+}
+
+void cg_plan_destroy(cg_plan_t p)
+{
+    if (!p) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    free_tables(p->d);
+    cudaSetDevice(prev);
+    delete p;
+}
+
+cg_status cg_plan_describe(cg_plan_t p, cg_plan_info* info, int* bins_host)
+{
+    if (!p || !info) return fail(CG_ERR_ARG, "plan or info is NULL");
+    std::memset(info, 0, sizeof(*info));
+    info->frame_len = p->N;
+    info->n_teeth = p->T;
+    info->fft_kind = p->kind;
+    info->coset_modulus = p->M;
+    info->coset_residue = p->r0;
+    info->fft_len = p->L;
+    info->n_radices = static_cast<int>(p->radices.size());
+    for (int i = 0; i < info->n_radices && i < 8; ++i) info->radices[i] = p->radices[i];
+    info->frames_per_cta = p->F;
+    info->lanes_per_frame = p->G;
+    info->n_collisions = p->n_collisions;
+    info->fused = p->opts.fused;
+    if (bins_host) std::memcpy(bins_host, p->bins.data(), sizeof(int) * p->T);
+    return CG_OK;
+}
+
+cg_status cg_set_reference(cg_plan_t p, const double* ref)
+{
+    if (!p || !ref) return fail(CG_ERR_ARG, "plan or ref is NULL");
+    for (int k = 0; k < p->T; ++k)
+        if (!(ref[k] > 0.0) || !std::isfinite(ref[k])) return fail(CG_ERR_ARG, "ref_spectrum[%d] must be > 0", k);
+    p->ref.assign(ref, ref + p->T);
+    std::vector<float> iref = inv_ref_of(p->ref);
+    cudaError_t e = cudaMemcpy(p->d.inv_ref, iref.data(), sizeof(float) * p->T, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "reference upload");
+    return CG_OK;
+}
+
+static cg_status check_frames(const cg_plan_s* p, const int16_t* frames, int64_t n)
+{
+    if (!p) return fail(CG_ERR_ARG, "plan is NULL");
+    if (n < 0) return fail(CG_ERR_ARG, "n_frames < 0");
+    if (n > 0 && !frames) return fail(CG_ERR_ARG, "frames_dev is NULL");
+    if (reinterpret_cast<uintptr_t>(frames) & 1) return fail(CG_ERR_ARG, "frames_dev must be 2-byte aligned");
+    if (n > (int64_t(1) << 40) / p->N) return fail(CG_ERR_ARG, "n_frames too large");
+    return CG_OK;
+}
+
+cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps, float* y,
+                     float* params, float* rss, int16_t* iters, int16_t* status, void* stream)
+{
+    cg_status st = check_frames(p, frames, n);
+    if (st != CG_OK) return st;
+    if (n == 0) return CG_OK;
+    if (!amps || !params) return fail(CG_ERR_ARG, "amps_dev and params_dev are required");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (p->opts.fused) {
+        e = cg::launch_fused(p, frames, n, amps, y, params, rss, iters, status, s);
+    } else {
+        e = cg::launch_readout(p, frames, n, amps, y, s);
+        // without y_dev the fit reads the magnitudes and applies the reference itself
+        if (e == cudaSuccess) e = cg::launch_fit(p, y, amps, n, nullptr, params, rss, iters, status, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cg_process launch");
+    return CG_OK;
+}
+
+cg_status cg_readout(cg_plan_t p, const int16_t* frames, int64_t n, float* amps, float* y, void* stream)
+{
+    cg_status st = check_frames(p, frames, n);
+    if (st != CG_OK) return st;
+    if (n == 0) return CG_OK;
+    if (!amps && !y) return fail(CG_ERR_ARG, "amps_dev and y_dev are both NULL");
+    cudaError_t e = cg::launch_readout(p, frames, n, amps, y, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cg_readout launch");
+    return CG_OK;
+}
+
+cg_status cg_fit(cg_plan_t p, const float* y, int64_t n, const float* p0, float* params, float* rss,
+                 int16_t* iters, int16_t* status, void* stream)
+{
+    if (!p) return fail(CG_ERR_ARG, "plan is NULL");
+    if (n < 0) return fail(CG_ERR_ARG, "n < 0");
+    if (n == 0) return CG_OK;
+    if (!y || !params) return fail(CG_ERR_ARG, "y_dev and params_dev are required");
+    cudaError_t e = cg::launch_fit(p, y, nullptr, n, p0, params, rss, iters, status, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cg_fit launch");
+    return CG_OK;
+}
+
+cg_status cg_reference_accumulate(cg_plan_t p, const int16_t* frames, int64_t n, double* ref_host,
+                                  void* stream)
+{
+    cg_status st = check_frames(p, frames, n);
+    if (st != CG_OK) return st;
+    if (n < 1) return fail(CG_ERR_ARG, "need at least one reference frame");
+    if (!ref_host) return fail(CG_ERR_ARG, "ref_host is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cg::launch_reference(p, frames, n, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ref_host, p->d.ref_out, sizeof(double) * p->T, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cg_reference_accumulate");
+    return CG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// cg_internal.h -- plan layout and kernel argument blocks shared by the
+// library's translation units (not part of the public ABI).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/combgpu.h"
+#include "cg_fit.cuh"
+
+namespace cg {
+
+constexpr int kMaxStages = 8;
+constexpr int kMinN = 8;
+constexpr int kMaxN = 16384;
+constexpr int kMinT = 5;
+constexpr int kMaxT = 1024;
+constexpr int kThreads = 256;
+
+// Arguments of the readout kernels (cast -> shared-memory FFT -> tooth read).
+struct ReadoutArgs {
+    const int16_t* frames;
+    int64_t n_frames;
+    int N, T, L, M, r0, kind, nst;
+    int radix[kMaxStages];
+    int F;            // frames per batch of one thread block
+    int fstride;      // complex elements per frame in the work buffers
+    int ystride;      // floats per frame of the shared normalised spectra
+    const float2* tw_L;    // [L]  W_L^m
+    const float2* tw_M;    // [M]  W_M^{r n2}        (coset)
+    const float2* tw_n1;   // [L]  W_N^{r n1}        (coset)
+    const float2* tw_b;    // [T]  W_N^{b_k}         (full)
+    const int* zidx;       // [T]  coset: m_k; full: b_k
+    const float* inv_ref;  // [T]
+    const float* u;        // [T]  normalised abscissa (fused fit)
+    float* amps;           // [n][T] or null
+    float* y;              // [n][T] or null
+    double* ref_part;      // reference mode: per-block partial sums [grid][T]
+    // shared-memory layout (byte offsets)
+    int sm_twL, sm_twM, sm_twn1, sm_twb, sm_zidx, sm_iref, sm_u;
+    int sm_raw, sm_a, sm_b, sm_y, sm_acc, sm_total;
+};
+
+struct DevTables {
+    float2* tw_L = nullptr;
+    float2* tw_M = nullptr;
+    float2* tw_n1 = nullptr;
+    float2* tw_b = nullptr;
+    int* zidx = nullptr;
+    float* inv_ref = nullptr;
+    float* u = nullptr;
+    int* outer_idx = nullptr;
+    double* ref_part = nullptr;   // [ref_part_rows][T]
+    double* ref_out = nullptr;    // [T]
+    int ref_part_rows = 0;
+};
+
+}  // namespace cg
+
+struct cg_plan_s {
+    int device = 0;
+    int num_sms = 0;
+    double fs = 0;
+    int N = 0, T = 0;
+    cg_opts opts{};
+    std::vector<int> bins;
+    std::vector<double> x, ref;
+    double x_mid = 0, x_scale = 1;
+    int kind = CG_FFT_FULL, M = 2, r0 = 0, L = 0;
+    std::vector<int> radices;
+    int F = 1;               // frames per batch
+    int G = 8;               // lanes per frame
+    int n_collisions = 0;
+    int n_outer = 0;
+    float u_mid = 0, du = 1, span = 1;
+    cg::DevTables d;
+    int grid_readout = 0, grid_fused = 0, grid_fit = 0;
+    cg::ReadoutArgs ra{};
+};
+
+namespace cg {
+
+// launchers (cg_kernels.cu)
+cudaError_t configure_kernels(cg_plan_s* p);
+cudaError_t launch_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps,
+                           float* y, cudaStream_t s);
+cudaError_t launch_fused(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps,
+                         float* y, float* params, float* rss, int16_t* iters, int16_t* status,
+                         cudaStream_t s);
+cudaError_t launch_fit(const cg_plan_s* p, const float* y, const float* amps, int64_t n,
+                       const float* p0, float* params, float* rss, int16_t* iters,
+                       int16_t* status, cudaStream_t s);
+cudaError_t launch_reference(const cg_plan_s* p, const int16_t* frames, int64_t n, cudaStream_t s);
+
+FitArgs make_fit_args(const cg_plan_s* p);
+
+}  // namespace cg

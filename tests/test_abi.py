@@ -1,0 +1,77 @@
+"""The C ABI library loads without a GPU and exports every declared symbol;
+host-side argument checks answer before any CUDA call (CPU only)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2307_12988_gb300 as cg
+from paper_2307_12988_gb300 import _binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(cg_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = cg.load()
+    declared = _declared_functions()
+    assert declared, "no declarations found"
+    missing = [n for n in declared if not hasattr(lib, n)]
+    assert not missing, missing
+    # and the binding marshals every one of them
+    assert set(declared) <= set(_binding.exported_symbols()) | {"cg_opts_default"}
+
+
+def test_status_strings_and_version():
+    assert cg.cg_version() == 100
+    assert cg.cg_status_string(0) == "ok"
+    assert "argument" in cg.cg_status_string(1)
+    assert cg.cg_status_string(99) == "unknown status"
+
+
+def test_defaults():
+    o = cg.cg_opts_default()
+    assert (o.max_iter, o.tol, o.lambda0, o.fused) == (20, 1e-6, 1e-3, 1)
+
+
+@pytest.mark.parametrize("kw,err", [
+    (dict(frame_len=7), "frame_len"),
+    (dict(frame_len=20000), "frame_len"),
+    (dict(tooth_freqs=np.array([1e6, 2e6, 3e6])), "n_teeth"),
+    (dict(sample_rate=-1.0), "sample_rate"),
+    (dict(ref=np.array([1.0, 1.0, 0.0, 1.0, 1.0])), "ref_spectrum"),
+    (dict(tooth_freqs=np.array([1e6, np.nan, 3e6, 4e6, 5e6])), "tooth_freqs"),
+    (dict(opts=dict(lanes_per_frame=5)), "lanes_per_frame"),
+    (dict(opts=dict(max_iter=-1)), "max_iter"),
+])
+def test_plan_argument_errors_before_cuda(kw, err):
+    args = dict(sample_rate=1e9, frame_len=1000,
+                tooth_freqs=np.array([11e6, 21e6, 31e6, 41e6, 51e6]), ref=None, opts={})
+    args.update(kw)
+    opts = cg.cg_opts_default(**args.pop("opts"))
+    with pytest.raises(cg.CgError) as ei:
+        cg.cg_plan(args["sample_rate"], args["frame_len"], args["tooth_freqs"], None,
+                   args["ref"], opts)
+    assert ei.value.status == 1
+    assert err in str(ei.value)
+
+
+def test_null_arguments_rejected():
+    lib = cg.load()
+    assert lib.cg_plan(None, 1e9, 1000, 5, None, None, None, None) == 1
+    assert lib.cg_process(None, None, 0, None, None, None, None, None, None, None) == 1
+    assert lib.cg_fit(None, None, 1, None, None, None, None, None, None) == 1
+    assert lib.cg_plan_describe(None, None, None) == 1

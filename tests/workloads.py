@@ -1,0 +1,44 @@
+"""Seeded workloads shared by the parity tests (test helper, not a test file).
+
+Each workload is built from ``synth`` (inputs) and ``oracle`` (reference
+spectrum and expected values); nothing here comes from the CUDA path."""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+
+import oracle
+import synth
+
+FS12 = synth.FULL_SCALE
+
+# name -> (geometry, frames, reference frames, generator keywords)
+SPECS = {
+    "tiny": (synth.TINY, 1000, 1000, dict(sigma=0.01 * FS12, center_amp_hz=5e6)),
+    "tiny_peak": (synth.TINY, 300, 300, dict(sigma=0.01 * FS12, center_amp_hz=5e6, shape="peak")),
+    "paper_rate": (synth.PAPER_RATE, 1500, 1000, dict(snr_db=30.0, center_amp_hz=20e6)),
+    "wide": (synth.WIDE, 400, 400, dict(snr_db=30.0, center_amp_hz=20e6)),
+    "serve4096": (synth.SERVE_4096, 200, 300, dict(snr_db=30.0, center_amp_hz=20e6)),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def workload(name: str) -> dict:
+    geom, n, n_ref, kw = SPECS[name]
+    seed = synth.BASE_SEED + sorted(SPECS).index(name)
+    stream = synth.make_stream(geom, seed)
+    fr = synth.frames(stream, n, **kw)
+    ref_kw = {k: v for k, v in kw.items() if k in ("sigma", "snr_db")}
+    rf = synth.frames(stream, n_ref, cavity=False, noise_stream=1, **ref_kw)
+    bins = oracle.tooth_bins(geom.sample_rate, geom.frame_len, geom.tooth_freqs)
+    ref = oracle.reference(rf["frames"], bins)
+    out = oracle.process(fr["frames"], bins, ref, geom.tooth_x)
+    conv = oracle.fit_batch(out["y"], geom.tooth_x, converged=True)
+    return dict(name=name, geom=geom, frames=fr["frames"], centers=fr["centers"],
+                ref_frames=rf["frames"], bins=bins, ref=ref, oracle=out, converged=conv)
+
+
+def plan_args(w: dict) -> tuple:
+    g = w["geom"]
+    return (g.sample_rate, g.frame_len, g.tooth_freqs, g.tooth_x, w["ref"])
