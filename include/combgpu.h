@@ -175,6 +175,32 @@ cg_status cg_fit(cg_plan_t plan, const float* y_dev, int64_t n, const float* p0_
 cg_status cg_reference_accumulate(cg_plan_t plan, const int16_t* frames_dev, int64_t n,
                                   double* ref_host, void* cuda_stream);
 
+/*
+ * cg_reference_accumulate_noalloc -- the same average as
+ * cg_reference_accumulate, for callers that cannot allocate device memory at
+ * the moment they need it: a real-time acquisition loop that must never
+ * wait on the allocator, a process whose device memory is held by a pool it
+ * does not own, or a host application that lends the library only a stream
+ * and buffers.  The paper has no counterpart; this is a convenience of the
+ * library's interface.
+ *   frames_dev  int16 [n][N] cavity-free frames on the plan's device, n >= 1
+ *   ref_dev     double [n_teeth] on the plan's device, 8-byte aligned:
+ *               receives mean |X_{b_k}| (the caller owns it)
+ * Allocates nothing and calls no allocating routine.  Its scratch is one array
+ * of 32768 doubles (256 KiB) compiled into the library, present on every GPU
+ * that loads it until the process exits; each call uses at most
+ * floor(32768 / n_teeth) thread blocks, and a plan whose n_teeth exceeds
+ * 32768 would be rejected with CG_ERR_ARG.  Every call shares that array:
+ * two calls whose work overlaps on the GPU (other streams, other threads)
+ * race and give wrong results, so serialise them.  Each call writes every
+ * scratch value it reads, so nothing needs clearing between calls.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Asynchronous on
+ * cuda_stream; errors: CG_ERR_ARG, CG_ERR_UNSUPPORTED, CG_ERR_CUDA.
+ */
+cg_status cg_reference_accumulate_noalloc(cg_plan_t plan, const int16_t* frames_dev,
+                                          int64_t n, double* ref_dev, void* cuda_stream);
+
 /* Text of a status code (static storage). */
 const char* cg_status_string(cg_status status);
 

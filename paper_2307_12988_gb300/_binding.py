@@ -65,6 +65,7 @@ _SIGS = {
     "cg_readout": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     "cg_fit": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
     "cg_reference_accumulate": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    "cg_reference_accumulate_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     "cg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cg_last_error": (ctypes.c_char_p, []),
     "cg_version": (ctypes.c_int, []),
@@ -202,6 +203,14 @@ def cg_reference_accumulate(plan: int, frames, n: int, stream=None) -> np.ndarra
     _check(load().cg_reference_accumulate(plan, _ptr(frames), int(n), _ptr(ref),
                                           _stream(stream)), "cg_reference_accumulate")
     return ref
+
+
+def cg_reference_accumulate_noalloc(plan: int, frames, n: int, ref_dev, stream=None) -> None:
+    """Reference average into the caller's device buffer ``ref_dev`` (float64
+    [n_teeth]) without any allocation by the library (see the C header)."""
+    _check(load().cg_reference_accumulate_noalloc(plan, _ptr(frames), int(n), _ptr(ref_dev),
+                                                  _stream(stream)),
+           "cg_reference_accumulate_noalloc")
 
 
 def cg_status_string(status: int) -> str:

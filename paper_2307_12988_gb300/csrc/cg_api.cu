@@ -128,6 +128,8 @@ std::vector<float> inv_ref_of(const std::vector<double>& ref)
 
 }  // namespace
 
+void cg::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 extern "C" {
 
 void cg_opts_default(cg_opts* o)

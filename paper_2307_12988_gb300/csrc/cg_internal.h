@@ -92,7 +92,14 @@ cudaError_t launch_fit(const cg_plan_s* p, const float* y, const float* amps, in
                        const float* p0, float* params, float* rss, int16_t* iters,
                        int16_t* status, cudaStream_t s);
 cudaError_t launch_reference(const cg_plan_s* p, const int16_t* frames, int64_t n, cudaStream_t s);
+// reference accumulation with caller-chosen scratch (max_rows partial rows of
+// T doubles) and output (T doubles), both device memory
+cudaError_t launch_reference_into(const cg_plan_s* p, const int16_t* frames, int64_t n,
+                                  double* part, int max_rows, double* out, cudaStream_t s);
 
 FitArgs make_fit_args(const cg_plan_s* p);
+
+// sets the thread-local text returned by cg_last_error()
+void set_last_error(const char* msg);
 
 }  // namespace cg

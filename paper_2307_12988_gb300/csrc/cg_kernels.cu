@@ -416,4 +416,26 @@ cudaError_t launch_reference(const cg_plan_s* p, const int16_t* frames, int64_t 
     return cudaGetLastError();
 }
 
+cudaError_t launch_reference_into(const cg_plan_s* p, const int16_t* frames, int64_t n,
+                                  double* part, int max_rows, double* out, cudaStream_t s)
+{
+    ReadoutArgs a = p->ra;
+    a.frames = frames;
+    a.n_frames = n;
+    a.amps = nullptr;
+    a.y = nullptr;
+    a.ref_part = part;
+    FitArgs fa = make_fit_args(p);
+    int grid = grid_for(n, a.F, p->grid_readout);
+    if (grid > max_rows) grid = max_rows;
+    void* args[] = {&a, &fa};
+    cudaError_t e = cudaLaunchKernel(readout_ptr(2, p->G), dim3(grid), dim3(kThreads), args,
+                                     a.sm_total, s);
+    if (e != cudaSuccess) return e;
+    const int tb = 128;
+    ref_reduce_kernel<<<(p->T + tb - 1) / tb, tb, 0, s>>>(part, grid, p->T,
+                                                          1.0 / static_cast<double>(n), out);
+    return cudaGetLastError();
+}
+
 }  // namespace cg
