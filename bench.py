@@ -148,6 +148,15 @@ def cpu_baseline_leg(frames, params, status, iters, plan, ref, g, args) -> dict:
     return {"cpu_baseline": cpu, "fit_error": fe}
 
 
+def launches_per_step(plan, n) -> int:
+    """Kernels of this library that one cg_process call launches."""
+    path = plan.info["path"]
+    if path == 3:   # pipeline: a readout and a fit kernel per chunk
+        chunk = plan._opts.chunk_frames or 65536
+        return 2 * ((n + chunk - 1) // chunk)
+    return 1 if path == 1 else 2
+
+
 def run_ours(args):
     import torch
     import paper_2307_12988_gb300 as cg
@@ -165,7 +174,7 @@ def run_ours(args):
     plan0.close()
     del ref_frames
     plan = cg.Plan(g.sample_rate, g.frame_len, g.tooth_freqs, g.tooth_x, ref,
-                   lanes_per_frame=args.lanes, fused=1 - args.unfused)
+                   lanes_per_frame=args.lanes, path=args.path, chunk_frames=args.chunk)
     T = plan.T
     amps = torch.empty((n, T), dtype=torch.float32, device=dev)
     params = torch.empty((n, 4), dtype=torch.float32, device=dev)
@@ -218,13 +227,14 @@ def run_ours(args):
                    "sample_rate_hz": g.sample_rate, "resident_bytes": 2 * g.frame_len * n,
                    "l2": "inputs (2.2 GB) larger than L2; no flush",
                    "lanes_per_frame": plan.info["lanes_per_frame"],
-                   "fused": plan.info["fused"], "fft_len": plan.info["fft_len"]},
+                   "path": ["auto", "fused", "split", "pipeline"][plan.info["path"]],
+                   "fft_len": plan.info["fft_len"]},
         "input_gbs": total_frames * 2 * g.frame_len / (ms_step / 1e3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_frame": bytes_per_frame},
-        "gpu_launches": args.steps * (1 if plan.info["fused"] else 2),
+        "gpu_launches": args.steps * launches_per_step(plan, n),
         "clocks": clocks,
     }
     torch.cuda.synchronize()
@@ -344,7 +354,8 @@ def main():
     ap.add_argument("--frames", type=int, default=1_000_000)
     ap.add_argument("--ref-frames", type=int, default=10_000)
     ap.add_argument("--lanes", type=int, default=0)
-    ap.add_argument("--unfused", type=int, default=0)
+    ap.add_argument("--path", type=int, default=0, help="0 auto, 1 fused, 2 split, 3 pipeline")
+    ap.add_argument("--chunk", type=int, default=0, help="frames per pipelined chunk (0: default)")
     ap.add_argument("--quick", action="store_true", help="skip fit check, CPU baseline and e2e")
     ap.add_argument("--check-frames", type=int, default=200_000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

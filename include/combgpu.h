@@ -60,6 +60,16 @@ typedef enum cg_status {
 enum { CG_READOUT_FFT = 0, CG_READOUT_GEMM_SPLIT = 1 };
 enum { CG_FFT_AUTO = 0, CG_FFT_FULL = 1, CG_FFT_COSET = 2 };
 enum { CG_INIT_MOMENT = 0, CG_INIT_MLP = 1 };
+/* Kernel arrangement of cg_process. */
+enum {
+    CG_PATH_AUTO = 0,      /* PIPELINE when the geometry admits it, else FUSED */
+    CG_PATH_FUSED = 1,     /* one kernel: readout and fit per thread block */
+    CG_PATH_SPLIT = 2,     /* a readout kernel, then a fit kernel */
+    CG_PATH_PIPELINE = 3   /* comb geometries (N = 10 P Q, teeth at +-r mod 10):
+                              fast readout and register-resident fit over chunks
+                              on two plan-owned streams, so memory streaming and
+                              fitting overlap */
+};
 
 /* Options of a plan.  Fill with cg_opts_default() and change what you need. */
 typedef struct cg_opts {
@@ -72,9 +82,9 @@ typedef struct cg_opts {
     double lambda0;       /* initial Marquardt damping; 1e-3 */
     int lanes_per_frame;  /* LM lanes cooperating on one frame: 4, 8, 16 or 32
                              (32 = one warp per frame); 0 = library default */
-    int fused;            /* 1 (default): readout and fit in one kernel;
-                             0: a readout kernel then a fit kernel */
-    int reserved[8];      /* must be zero */
+    int path;             /* CG_PATH_* (default CG_PATH_AUTO) */
+    int chunk_frames;     /* frames per pipelined chunk; 0 = 65536 */
+    int reserved[7];      /* must be zero */
 } cg_opts;
 
 typedef struct cg_plan_s* cg_plan_t;
@@ -92,11 +102,11 @@ typedef struct cg_plan_info {
     int frames_per_cta;   /* frames one thread block transforms at a time */
     int lanes_per_frame;  /* LM lanes per frame */
     int n_collisions;     /* pairs of teeth that read the same bin */
-    int fused;
+    int path;             /* CG_PATH_* that cg_process takes for aligned frames */
 } cg_plan_info;
 
 /* Fill *opts with the defaults (FFT readout, moment init, 20 iterations,
- * tol 1e-6, lambda0 1e-3, fused kernel).  opts must not be NULL. */
+ * tol 1e-6, lambda0 1e-3, CG_PATH_AUTO).  opts must not be NULL. */
 void cg_opts_default(cg_opts* opts);
 
 /*

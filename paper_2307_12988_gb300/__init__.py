@@ -16,7 +16,8 @@ from ._binding import (CgError, cg_fit, cg_opts_default, cg_plan, cg_plan_descri
                        cg_set_reference, cg_status_string, cg_version, load)
 from ._binding import (FFT_AUTO, FFT_COSET, FFT_FULL, FIT_CONVERGED, FIT_INIT_FLAT,
                        FIT_MAX_ITER, FIT_NONFINITE, FIT_SINGULAR, INIT_MLP, INIT_MOMENT,
-                       READOUT_FFT, READOUT_GEMM_SPLIT)
+                       READOUT_FFT, READOUT_GEMM_SPLIT, PATH_AUTO, PATH_FUSED, PATH_SPLIT,
+                       PATH_PIPELINE)
 
 __all__ = ["Plan", "CgError", "load", "cg_plan", "cg_plan_destroy", "cg_plan_describe",
            "cg_process", "cg_readout", "cg_fit", "cg_reference_accumulate",

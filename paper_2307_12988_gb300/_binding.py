@@ -27,6 +27,7 @@ FIT_CONVERGED, FIT_MAX_ITER, FIT_SINGULAR, FIT_NONFINITE, FIT_INIT_FLAT = 0, 1, 
 READOUT_FFT, READOUT_GEMM_SPLIT = 0, 1
 FFT_AUTO, FFT_FULL, FFT_COSET = 0, 1, 2
 INIT_MOMENT, INIT_MLP = 0, 1
+PATH_AUTO, PATH_FUSED, PATH_SPLIT, PATH_PIPELINE = 0, 1, 2, 3
 
 
 class CgError(RuntimeError):
@@ -41,7 +42,8 @@ class cg_opts(ctypes.Structure):
     _fields_ = [("readout", ctypes.c_int), ("fft", ctypes.c_int), ("init", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
                 ("lambda0", ctypes.c_double), ("lanes_per_frame", ctypes.c_int),
-                ("fused", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("path", ctypes.c_int), ("chunk_frames", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 class cg_plan_info(ctypes.Structure):
@@ -50,7 +52,7 @@ class cg_plan_info(ctypes.Structure):
                 ("coset_residue", ctypes.c_int), ("fft_len", ctypes.c_int),
                 ("n_radices", ctypes.c_int), ("radices", ctypes.c_int * 8),
                 ("frames_per_cta", ctypes.c_int), ("lanes_per_frame", ctypes.c_int),
-                ("n_collisions", ctypes.c_int), ("fused", ctypes.c_int)]
+                ("n_collisions", ctypes.c_int), ("path", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -116,7 +116,100 @@ void free_tables(cg::DevTables& d)
     cudaFree(d.outer_idx);
     cudaFree(d.ref_part);
     cudaFree(d.ref_out);
+    cudaFree(d.tw_M5);
+    cudaFree(d.tooth_of_m);
     d = cg::DevTables{};
+}
+
+void free_plan(cg_plan_s* p)
+{
+    free_tables(p->d);
+    if (p->s_read) cudaStreamDestroy(p->s_read);
+    if (p->s_fit) cudaStreamDestroy(p->s_fit);
+    for (cudaEvent_t e : {p->ev_fork, p->ev_read, p->ev_join_r, p->ev_join_f})
+        if (e) cudaEventDestroy(e);
+    delete p;
+}
+
+// Throughput path: fast readout (N = 10 Q' with L = 10 Q) and the
+// register-resident LM.  Chooses the batch size, shared-memory layout, lane
+// group and launch grids; leaves fast_ok false when the geometry does not fit.
+cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
+{
+    p->fast_ok = false;
+    const int N = p->N, T = p->T, L = p->L;
+    if (p->kind != CG_FFT_COSET || p->M != 10 || L % 10 != 0) return cudaSuccess;
+    const int Q = L / 10;
+    if (!cg::fast_readout_ptr(Q)) return cudaSuccess;
+    std::vector<int> tom(L, -1);
+    for (int k = 0; k < T; ++k) {
+        if (tom[zidx[k]] >= 0) return cudaSuccess;   // two teeth on one bin: generic path
+        tom[zidx[k]] = k;
+    }
+    int G = p->opts.lanes_per_frame ? p->opts.lanes_per_frame : 4;
+    int ppl = cg::fit2_ppl(G, T);
+    while (ppl == 0 && G < 32 && !p->opts.lanes_per_frame) ppl = cg::fit2_ppl(G *= 2, T);
+    if (ppl == 0) return cudaSuccess;
+    // batch size: minimise idle thread slots of the two transform stages
+    // (stage 1: 10 items per frame, cost ~ 50 Q; stage 2: Q items, cost ~ 200)
+    int bestF = 2;
+    double best = 1e30;
+    for (int F = 2; F <= 32; ++F) {
+        const int bytes = 2 * N * F + 32 + 8 * L * F + 8 * T * F;
+        if (bytes > 96 * 1024) break;
+        const double cost = (std::ceil(10.0 * F / 128.0) * 50.0 * Q + std::ceil(double(Q) * F / 128.0) * 200.0) / F;
+        if (cost < best - 1e-9) { best = cost; bestF = F; }
+    }
+    cg::FastArgs& a = p->fa;
+    a.N = N;
+    a.T = T;
+    a.F = bestF;
+    a.pair_isign = (p->r0 & 1) ? -1 : 1;
+    int off = 0;
+    a.sm_twL = off; off = align16(off + 8 * L);
+    a.sm_twN = off; off = align16(off + 8 * L);
+    a.sm_tom = off; off = align16(off + 4 * L);
+    a.sm_iref = off; off = align16(off + 4 * T);
+    a.sm_u = off; off = align16(off + 4 * T);
+    a.sm_raw = off; off = align16(off + 2 * N * bestF + 32);
+    a.sm_Y = off; off = align16(off + 8 * L * bestF);
+    a.sm_amps = off; off = align16(off + 4 * T * bestF);
+    a.sm_y = off; off = align16(off + 4 * T * bestF);
+    a.sm_total = off;
+    std::vector<float2> tw5(5);
+    for (int j = 0; j < 5; ++j) {
+        const double ang = -kTwoPi * static_cast<double>((p->r0 * j) % 10) / 10.0;
+        tw5[j] = make_float2(static_cast<float>(std::cos(ang)), static_cast<float>(std::sin(ang)));
+    }
+    cudaError_t e;
+    if ((e = upload(&p->d.tw_M5, tw5)) != cudaSuccess) return e;
+    if ((e = upload(&p->d.tooth_of_m, tom)) != cudaSuccess) return e;
+    a.twL = p->d.tw_L;
+    a.twN = p->d.tw_n1;
+    a.twM = p->d.tw_M5;
+    a.tooth_of_m = p->d.tooth_of_m;
+    a.inv_ref = p->d.inv_ref;
+    a.u = p->d.u;
+    void* fr = cg::fast_readout_ptr(Q);
+    if ((e = cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, a.sm_total)) != cudaSuccess) return e;
+    int occ = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fr, 128, a.sm_total)) != cudaSuccess) return e;
+    if (occ < 1) return cudaSuccess;
+    p->grid_fast = p->num_sms * occ;
+    void* ff = cg::fit2_ptr(G, ppl);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ff, 256, 0)) != cudaSuccess) return e;
+    if (occ < 1) return cudaSuccess;
+    p->grid_fit2 = p->num_sms * occ;
+    if ((e = cudaStreamCreateWithFlags(&p->s_read, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaStreamCreateWithFlags(&p->s_fit, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    for (cudaEvent_t* ev : {&p->ev_fork, &p->ev_read, &p->ev_join_r, &p->ev_join_f})
+        if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    p->Q = Q;
+    p->G2 = G;
+    p->PPL = ppl;
+    p->chunk = p->opts.chunk_frames ? p->opts.chunk_frames : 65536;
+    p->fast_ok = true;
+    return cudaSuccess;
 }
 
 std::vector<float> inv_ref_of(const std::vector<double>& ref)
@@ -143,7 +236,8 @@ void cg_opts_default(cg_opts* o)
     o->tol = 1e-6;
     o->lambda0 = 1e-3;
     o->lanes_per_frame = 0;
-    o->fused = 1;
+    o->path = CG_PATH_AUTO;
+    o->chunk_frames = 0;
 }
 
 const char* cg_status_string(cg_status s)
@@ -185,9 +279,11 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
     if (o.lanes_per_frame != 0 && o.lanes_per_frame != 4 && o.lanes_per_frame != 8 &&
         o.lanes_per_frame != 16 && o.lanes_per_frame != 32)
         return fail(CG_ERR_ARG, "lanes_per_frame must be 0, 4, 8, 16 or 32");
+    if (o.path < CG_PATH_AUTO || o.path > CG_PATH_PIPELINE) return fail(CG_ERR_ARG, "path must be a CG_PATH_* value");
+    if (o.chunk_frames < 0) return fail(CG_ERR_ARG, "chunk_frames must be >= 0");
     if (o.readout != CG_READOUT_FFT) return fail(CG_ERR_UNSUPPORTED, "readout kind %d not available", o.readout);
     if (o.init != CG_INIT_MOMENT) return fail(CG_ERR_UNSUPPORTED, "init kind %d not available", o.init);
-    for (int i = 0; i < 8; ++i)
+    for (size_t i = 0; i < sizeof(o.reserved) / sizeof(o.reserved[0]); ++i)
         if (o.reserved[i] != 0) return fail(CG_ERR_ARG, "reserved option fields must be zero");
 
     auto* p = new cg_plan_s();
@@ -357,6 +453,10 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         delete p;
         return cuda_fail(e, "reference scratch");
     }
+    if ((e = setup_fast(p, zidx)) != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "throughput path set-up");
+    }
     *out = p;
     return CG_OK;
 }
@@ -368,9 +468,8 @@ void cg_plan_destroy(cg_plan_t p)
     cudaGetDevice(&prev);
     cudaSetDevice(p->device);
     cudaDeviceSynchronize();
-    free_tables(p->d);
+    free_plan(p);
     cudaSetDevice(prev);
-    delete p;
 }
 
 cg_status cg_plan_describe(cg_plan_t p, cg_plan_info* info, int* bins_host)
@@ -388,7 +487,9 @@ cg_status cg_plan_describe(cg_plan_t p, cg_plan_info* info, int* bins_host)
     info->frames_per_cta = p->F;
     info->lanes_per_frame = p->G;
     info->n_collisions = p->n_collisions;
-    info->fused = p->opts.fused;
+    info->path = (p->opts.path == CG_PATH_AUTO) ? (p->fast_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED)
+               : (p->opts.path == CG_PATH_PIPELINE && !p->fast_ok) ? CG_PATH_FUSED : p->opts.path;
+    if (info->path == CG_PATH_PIPELINE) info->lanes_per_frame = p->G2;
     if (bins_host) std::memcpy(bins_host, p->bins.data(), sizeof(int) * p->T);
     return CG_OK;
 }
@@ -424,7 +525,36 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
     if (!amps || !params) return fail(CG_ERR_ARG, "amps_dev and params_dev are required");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
-    if (p->opts.fused) {
+    int path = p->opts.path;
+    if (path == CG_PATH_AUTO) path = p->fast_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED;
+    // the fast readout reads sample pairs as 32-bit words: frames 4-byte aligned
+    if (path == CG_PATH_PIPELINE && (!p->fast_ok || (reinterpret_cast<uintptr_t>(frames) & 3)))
+        path = CG_PATH_FUSED;
+    if (path == CG_PATH_PIPELINE) {
+        // fork onto the plan's two streams; chunk c is read out on s_read while
+        // chunk c-1 is fitted on s_fit (the readout leaves each frame's moment
+        // initial guess in params and its flag in status for the fit)
+        e = cudaEventRecord(p->ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_read, p->ev_fork, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_fit, p->ev_fork, 0);
+        for (int64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += p->chunk) {
+            const int64_t m = (n - c0) < p->chunk ? (n - c0) : p->chunk;
+            const int64_t T = p->T;
+            e = cg::launch_fast_readout(p, frames + c0 * p->N, m, amps + c0 * T, y ? y + c0 * T : nullptr,
+                                        params + c0 * 4, status ? status + c0 : nullptr, p->s_read);
+            if (e == cudaSuccess) e = cudaEventRecord(p->ev_read, p->s_read);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_fit, p->ev_read, 0);
+            if (e == cudaSuccess)
+                e = cg::launch_fit2(p, y ? y + c0 * T : nullptr, amps + c0 * T, m, params + c0 * 4,
+                                    status ? status + c0 : nullptr, params + c0 * 4,
+                                    rss ? rss + c0 : nullptr, iters ? iters + c0 : nullptr,
+                                    status ? status + c0 : nullptr, p->s_fit);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_join_r, p->s_read);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_join_f, p->s_fit);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join_r, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join_f, 0);
+    } else if (path == CG_PATH_FUSED) {
         e = cg::launch_fused(p, frames, n, amps, y, params, rss, iters, status, s);
     } else {
         e = cg::launch_readout(p, frames, n, amps, y, s);

@@ -176,6 +176,53 @@ template <> struct Dft<7> : DftOdd<7> {};
 template <> struct Dft<11> : DftOdd<11> {};
 template <> struct Dft<13> : DftOdd<13> {};
 
+// composite R = R1 * R2 in registers (decimation in time, n = R2 n1 + n2,
+// k = k1 + R1 k2):  X[k1 + R1 k2] =
+//   sum_{n2} W_R2^{n2 k2} W_R^{n2 k1} sum_{n1} a[R2 n1 + n2] W_R1^{n1 k1}
+template <int R1, int R2>
+struct DftComposite {
+    static constexpr int R = R1 * R2;
+    static __device__ __forceinline__ void run(float2 (&a)[R])
+    {
+        constexpr RootTable<R> tab{};
+        float2 B[R2][R1];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) {
+            float2 v[R1];
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) v[n1] = a[R2 * n1 + n2];
+            Dft<R1>::run(v);
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) {
+                const int e = (n2 * k1) % R;
+                if (e == 0) {
+                    B[n2][k1] = v[k1];
+                } else {
+                    // W_R^e = cos(2 pi e/R) - i sin(2 pi e/R)
+                    const float c = tab.c[e], s = tab.s[e];
+                    B[n2][k1] = make_float2(fmaf(v[k1].x, c, v[k1].y * s), fmaf(v[k1].y, c, -v[k1].x * s));
+                }
+            }
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            float2 w[R2];
+#pragma unroll
+            for (int n2 = 0; n2 < R2; ++n2) w[n2] = B[n2][k1];
+            Dft<R2>::run(w);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) a[k1 + R1 * k2] = w[k2];
+        }
+    }
+};
+template <> struct Dft<6> : DftComposite<2, 3> {};
+template <> struct Dft<10> : DftComposite<2, 5> {};
+template <> struct Dft<12> : DftComposite<4, 3> {};
+template <> struct Dft<16> : DftComposite<4, 4> {};
+template <> struct Dft<20> : DftComposite<4, 5> {};
+template <> struct Dft<22> : DftComposite<2, 11> {};
+template <> struct Dft<25> : DftComposite<5, 5> {};
+
 // ---------------------------------------------------------------------------
 // One Stockham stage of radix R over F frames in shared memory.
 //   Ns = product of the radices of the earlier stages.

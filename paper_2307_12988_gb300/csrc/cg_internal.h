@@ -42,7 +42,48 @@ struct ReadoutArgs {
     int sm_raw, sm_a, sm_b, sm_y, sm_acc, sm_total;
 };
 
+// Arguments of the fast readout (comb geometries, N = 10 P Q).
+struct FastArgs {
+    const int16_t* frames;
+    int64_t n_frames;
+    int N, T, F;
+    int pair_isign;          // (-1)^r: sign pairing x_j with x_{j+5} in the fold
+    const float2* twL;       // [L]  W_L^m
+    const float2* twN;       // [L]  W_N^{r n1}
+    const float2* twM;       // [5]  W_10^{r j}
+    const int* tooth_of_m;   // [L]  tooth reading Z[m], or -1
+    const float* inv_ref;    // [T]
+    const float* u;          // [T]
+    float* amps;             // [n][T] or null
+    float* y;                // [n][T] or null
+    float* p0_out;           // [n][4] starting parameters (abscissa units)
+    int16_t* flag_out;       // [n] initial-guess flags, or null
+    int sm_twL, sm_twN, sm_tom, sm_iref, sm_u, sm_raw, sm_Y, sm_amps, sm_y, sm_total;
+};
+
+// Arguments of the register-resident LM kernel.
+struct Fit2Args {
+    int64_t n;
+    int T;
+    int task;                // frames per warp task
+    const float* y;          // [n][T] normalised, or null
+    const float* amps;       // [n][T] magnitudes when y is null
+    const float* inv_ref;    // [T]
+    const float* u;          // [T]
+    const float* p0;         // [n][4] starting parameters (abscissa units)
+    const int16_t* flags_in; // [n] initial-guess flags or null
+    float x_mid, x_scale;
+    int max_iter;
+    float tol, lambda0;
+    float* params;
+    float* rss;
+    int16_t* iters;
+    int16_t* status;
+};
+
 struct DevTables {
+    float2* tw_M5 = nullptr;
+    int* tooth_of_m = nullptr;
     float2* tw_L = nullptr;
     float2* tw_M = nullptr;
     float2* tw_n1 = nullptr;
@@ -77,6 +118,16 @@ struct cg_plan_s {
     cg::DevTables d;
     int grid_readout = 0, grid_fused = 0, grid_fit = 0;
     cg::ReadoutArgs ra{};
+    // throughput path (fast readout + register-resident LM over chunks)
+    bool fast_ok = false;    // geometry admits the fast readout
+    int Q = 0;               // L = 10 Q
+    int G2 = 4;              // LM lanes per frame of the register-resident fit
+    int PPL = 0;             // LM points per lane
+    int grid_fast = 0, grid_fit2 = 0;
+    int64_t chunk = 0;       // frames per pipelined chunk
+    cg::FastArgs fa{};
+    cudaStream_t s_read = nullptr, s_fit = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_read = nullptr, ev_join_r = nullptr, ev_join_f = nullptr;
 };
 
 namespace cg {
@@ -98,6 +149,16 @@ cudaError_t launch_reference_into(const cg_plan_s* p, const int16_t* frames, int
                                   double* part, int max_rows, double* out, cudaStream_t s);
 
 FitArgs make_fit_args(const cg_plan_s* p);
+
+// throughput path (cg_fast.cu)
+void* fast_readout_ptr(int Q);
+void* fit2_ptr(int G, int PPL);
+int fit2_ppl(int G, int T);
+cudaError_t launch_fast_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps,
+                                float* y, float* p0_out, int16_t* flag_out, cudaStream_t s);
+cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, int64_t n,
+                        const float* p0, const int16_t* flags_in, float* params, float* rss,
+                        int16_t* iters, int16_t* status, cudaStream_t s);
 
 // sets the thread-local text returned by cg_last_error()
 void set_last_error(const char* msg);

@@ -44,7 +44,7 @@ def test_status_strings_and_version():
 
 def test_defaults():
     o = cg.cg_opts_default()
-    assert (o.max_iter, o.tol, o.lambda0, o.fused) == (20, 1e-6, 1e-3, 1)
+    assert (o.max_iter, o.tol, o.lambda0, o.path) == (20, 1e-6, 1e-3, 0)
 
 
 @pytest.mark.parametrize("kw,err", [

@@ -41,7 +41,7 @@ def _amp_err(amps, w):
 @pytest.mark.parametrize("fft", [cg.FFT_AUTO, cg.FFT_FULL])
 def test_readout_parity(dev, name, fft):
     w = W.workload(name)
-    with _plan(w, fft=fft, fused=0) as p:
+    with _plan(w, fft=fft, path=cg.PATH_SPLIT) as p:
         fr = torch.from_numpy(w["frames"]).to(dev)
         amps, y = p.readout(fr)
         torch.cuda.synchronize()
@@ -66,7 +66,7 @@ def test_coset_transform_is_chosen_for_comb_geometries():
 def test_readout_ragged_misaligned_and_empty(dev):
     w = W.workload("paper_rate")
     fr = torch.from_numpy(w["frames"]).to(dev)
-    with _plan(w, fused=0) as p:
+    with _plan(w, path=cg.PATH_SPLIT) as p:
         # odd first frame: the batch starts 8 bytes off a 16-byte boundary
         for a, b in [(1, 2), (1, 62), (3, 700), (0, 1), (997, 1500)]:
             amps, _ = p.readout(fr[a:b], want_y=False)
@@ -120,10 +120,10 @@ def test_lm_parity_from_oracle_init(dev, lanes):
 
 
 @pytest.mark.parametrize("name", ["tiny", "tiny_peak", "paper_rate", "wide", "serve4096"])
-@pytest.mark.parametrize("fused", [1, 0])
-def test_process_parity(dev, name, fused):
+@pytest.mark.parametrize("path", [cg.PATH_PIPELINE, cg.PATH_FUSED, cg.PATH_SPLIT])
+def test_process_parity(dev, name, path):
     w = W.workload(name)
-    with _plan(w, fused=fused) as p:
+    with _plan(w, path=path) as p:
         fr = torch.from_numpy(w["frames"]).to(dev)
         out = p.process(fr)
         torch.cuda.synchronize()
