@@ -146,16 +146,20 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
         if (tom[zidx[k]] >= 0) return cudaSuccess;   // two teeth on one bin: generic path
         tom[zidx[k]] = k;
     }
-    int G = p->opts.lanes_per_frame ? p->opts.lanes_per_frame : 4;
-    int ppl = cg::fit2_ppl(G, T);
-    while (ppl == 0 && G < 32 && !p->opts.lanes_per_frame) ppl = cg::fit2_ppl(G *= 2, T);
+    // LM lanes per frame: 4 unless a lane would hold more than 28 points
+    int G = p->opts.lanes_per_frame ? p->opts.lanes_per_frame : (T <= 112 ? 4 : 8);
+    bool exact = false;
+    int ppl = cg::fit2_ppl(G, T, &exact);
+    while (ppl == 0 && G < 32 && !p->opts.lanes_per_frame) ppl = cg::fit2_ppl(G *= 2, T, &exact);
     if (ppl == 0) return cudaSuccess;
+    const int npad = cg::init_npad(p->n_outer);
+    if (npad == 0) return cudaSuccess;
     // batch size: minimise idle thread slots of the two transform stages
     // (stage 1: 10 items per frame, cost ~ 50 Q; stage 2: Q items, cost ~ 200)
     int bestF = 2;
     double best = 1e30;
     for (int F = 2; F <= 32; ++F) {
-        const int bytes = 2 * N * F + 32 + 8 * L * F + 8 * T * F;
+        const int bytes = 2 * N * F + 32 + 8 * L * F + 4 * T * F;
         if (bytes > 96 * 1024) break;
         const double cost = (std::ceil(10.0 * F / 128.0) * 50.0 * Q + std::ceil(double(Q) * F / 128.0) * 200.0) / F;
         if (cost < best - 1e-9) { best = cost; bestF = F; }
@@ -170,12 +174,27 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
     a.sm_twN = off; off = align16(off + 8 * L);
     a.sm_tom = off; off = align16(off + 4 * L);
     a.sm_iref = off; off = align16(off + 4 * T);
-    a.sm_u = off; off = align16(off + 4 * T);
+    a.sm_u = 0;
     a.sm_raw = off; off = align16(off + 2 * N * bestF + 32);
     a.sm_Y = off; off = align16(off + 8 * L * bestF);
     a.sm_amps = off; off = align16(off + 4 * T * bestF);
-    a.sm_y = off; off = align16(off + 4 * T * bestF);
+    a.sm_y = 0;
     a.sm_total = off;
+    // lane-per-frame initial guess: tables + 4 warps x 32 staged rows
+    cg::InitArgs& ia = p->ia;
+    ia.T = T;
+    ia.row_stride = T | 1;
+    ia.n_outer = p->n_outer;
+    ia.inv_ref = p->d.inv_ref;
+    ia.u = p->d.u;
+    ia.outer_idx = p->d.outer_idx;
+    ia.u_mid = p->u_mid;
+    ia.du = p->du;
+    ia.span = p->span;
+    ia.x_mid = static_cast<float>(p->x_mid);
+    ia.x_scale = static_cast<float>(p->x_scale);
+    p->init_npad = npad;
+    p->init_smem = 4 * (2 * T + p->n_outer) + 4 * 4 * 32 * ia.row_stride;
     std::vector<float2> tw5(5);
     for (int j = 0; j < 5; ++j) {
         const double ang = -kTwoPi * static_cast<double>((p->r0 * j) % 10) / 10.0;
@@ -196,10 +215,16 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fr, 128, a.sm_total)) != cudaSuccess) return e;
     if (occ < 1) return cudaSuccess;
     p->grid_fast = p->num_sms * occ;
-    void* ff = cg::fit2_ptr(G, ppl);
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ff, 256, 0)) != cudaSuccess) return e;
+    void* ff = cg::fit2_ptr(G, ppl, exact);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ff, 256, 8 * T)) != cudaSuccess) return e;
     if (occ < 1) return cudaSuccess;
     p->grid_fit2 = p->num_sms * occ;
+    void* fi = cg::init_ptr(npad);
+    if ((e = cudaFuncSetAttribute(fi, cudaFuncAttributeMaxDynamicSharedMemorySize, p->init_smem)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fi, 128, p->init_smem)) != cudaSuccess) return e;
+    if (occ < 1) return cudaSuccess;
+    p->grid_init = p->num_sms * occ;
+    p->ppl_exact = exact;
     if ((e = cudaStreamCreateWithFlags(&p->s_read, cudaStreamNonBlocking)) != cudaSuccess) return e;
     if ((e = cudaStreamCreateWithFlags(&p->s_fit, cudaStreamNonBlocking)) != cudaSuccess) return e;
     for (cudaEvent_t* ev : {&p->ev_fork, &p->ev_read, &p->ev_join_r, &p->ev_join_f})
@@ -541,7 +566,10 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
             const int64_t m = (n - c0) < p->chunk ? (n - c0) : p->chunk;
             const int64_t T = p->T;
             e = cg::launch_fast_readout(p, frames + c0 * p->N, m, amps + c0 * T, y ? y + c0 * T : nullptr,
-                                        params + c0 * 4, status ? status + c0 : nullptr, p->s_read);
+                                        p->s_read);
+            if (e == cudaSuccess)
+                e = cg::launch_init(p, y ? y + c0 * T : nullptr, amps + c0 * T, m, params + c0 * 4,
+                                    status ? status + c0 : nullptr, p->s_read);
             if (e == cudaSuccess) e = cudaEventRecord(p->ev_read, p->s_read);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_fit, p->ev_read, 0);
             if (e == cudaSuccess)

@@ -40,31 +40,39 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Asynchronous staging of int16 elements [e0, e0 + ne) into raw: 16-byte
 // chunks aligned in global memory go by cp.async, the ragged head/tail chunk
 // by plain loads.  Returns the element offset of e0 inside raw.
+__device__ __forceinline__ void copy_partial_chunk(uintptr_t pa, int c, uintptr_t p, uintptr_t pend,
+                                                   int16_t* raw)
+{
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const uintptr_t ep = pa + 16 * static_cast<uintptr_t>(c) + 2 * e;
+        if (ep >= p && ep < pend) raw[8 * c + e] = *reinterpret_cast<const int16_t*>(ep);
+    }
+}
+
 __device__ __forceinline__ int stage_async(const int16_t* frames, int64_t e0, int64_t ne, int16_t* raw)
 {
-    const char* p = reinterpret_cast<const char*>(frames + e0);
-    const uintptr_t pa = reinterpret_cast<uintptr_t>(p) & ~static_cast<uintptr_t>(15);
-    const int off = static_cast<int>((reinterpret_cast<uintptr_t>(p) - pa) >> 1);
-    const char* pend = p + ne * 2;
-    const int64_t nchunks = (static_cast<int64_t>(reinterpret_cast<uintptr_t>(pend) - pa) + 15) >> 4;
-    for (int64_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
-        const char* cp = reinterpret_cast<const char*>(pa) + 16 * c;
-        if (cp >= p && cp + 16 <= pend) {
-            cp_async16(reinterpret_cast<char*>(raw) + 16 * c, cp);
-        } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const char* ep = cp + 2 * e;
-                if (ep >= p && ep < pend) raw[8 * c + e] = *reinterpret_cast<const int16_t*>(ep);
-            }
-        }
-    }
+    const uintptr_t p = reinterpret_cast<uintptr_t>(frames + e0);
+    const uintptr_t pa = p & ~static_cast<uintptr_t>(15);
+    const uintptr_t pend = p + static_cast<uintptr_t>(ne) * 2;
+    const int off = static_cast<int>((p - pa) >> 1);
+    const int nchunks = static_cast<int>((pend - pa + 15) >> 4);   // a batch is < 2 GiB
+    const int first_whole = (p == pa) ? 0 : 1;
+    const int end_whole = ((pend & 15) == 0) ? nchunks : nchunks - 1;   // whole chunks [first, end)
+    const char* src = reinterpret_cast<const char*>(pa);
+    char* dst = reinterpret_cast<char*>(raw);
+    for (int c = first_whole + static_cast<int>(threadIdx.x); c < end_whole; c += blockDim.x)
+        cp_async16(dst + 16 * c, src + 16 * c);
+    // ragged first and last chunk, element by element
+    if (threadIdx.x == 0 && first_whole == 1) copy_partial_chunk(pa, 0, p, pend, raw);
+    if (threadIdx.x == blockDim.x - 1 && end_whole < nchunks && !(nchunks == 1 && first_whole == 1))
+        copy_partial_chunk(pa, nchunks - 1, p, pend, raw);
     cp_async_commit();
     return off;
 }
 
 template <int P, int Q>
-__global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a, FitArgs fa)
+__global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
 {
     constexpr int L = P * Q;
     constexpr int MH = 5;                     // M / 2 with M = 10
@@ -73,21 +81,16 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a, FitArgs f
     float2* twN = reinterpret_cast<float2*>(sm + a.sm_twN);
     int* tom = reinterpret_cast<int*>(sm + a.sm_tom);
     float* iref = reinterpret_cast<float*>(sm + a.sm_iref);
-    float* us = reinterpret_cast<float*>(sm + a.sm_u);
     int16_t* raw = reinterpret_cast<int16_t*>(sm + a.sm_raw);
     float2* Yb = reinterpret_cast<float2*>(sm + a.sm_Y);
     float* amp_s = reinterpret_cast<float*>(sm + a.sm_amps);
-    float* y_s = reinterpret_cast<float*>(sm + a.sm_y);
     const int T = a.T, N = a.N, F = a.F;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         twL[i] = a.twL[i];
         twN[i] = a.twN[i];
         tom[i] = a.tooth_of_m[i];
     }
-    for (int i = threadIdx.x; i < T; i += blockDim.x) {
-        iref[i] = a.inv_ref[i];
-        us[i] = a.u[i];
-    }
+    for (int i = threadIdx.x; i < T; i += blockDim.x) iref[i] = a.inv_ref[i];
     // fold twiddles w_j = W_10^(r j): with s = (-1)^r, w_{5-j} = s conj(w_j), so
     // sum_j D_j w_j = D_0 + (E_1 c_1 + E_2 c_2) + i (F_1 s_1 + F_2 s_2) where
     // D_j = x_j + s x_{j+5}, E_j = D_j + s D_{5-j}, F_j = D_j - s D_{5-j}
@@ -158,38 +161,15 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a, FitArgs f
             }
         }
         __syncthreads();
-        // ---------------- outputs (coalesced) and normalised spectra ----------
-        for (int i = threadIdx.x; i < nf * T; i += blockDim.x) {
-            const int f = i / T;
-            const int k = i - f * T;
-            const float av = amp_s[i];
-            const float yv = av * iref[k];
-            y_s[i] = yv;
-            if (a.amps) a.amps[f0 * T + i] = av;
-            if (a.y) a.y[f0 * T + i] = yv;
-        }
-        __syncthreads();
-        // ---------------- moment initial guess, 8 lanes per frame -------------
+        // ---------------- outputs (coalesced) --------------------------------
         {
-            constexpr int GI = 8;
-            const int ngroups = blockDim.x / GI;
-            const int group = threadIdx.x / GI;
-            const int warp_first_group = (threadIdx.x & ~31) / GI;
-            for (int base = 0; base < nf; base += ngroups) {
-                if (base + warp_first_group >= nf) break;   // warp-uniform
-                const int fi = base + group;
-                const bool valid = fi < nf;
-                float p[4];
-                int flag = 0;
-                moment_init<GI>(y_s + (valid ? fi : 0) * T, us, fa, p, flag);
-                if (valid && (threadIdx.x & (GI - 1)) == 0) {
-                    float* po = a.p0_out + (f0 + fi) * 4;
-                    po[0] = fmaf(fa.x_scale, p[0], fa.x_mid);
-                    po[1] = fa.x_scale * fabsf(p[1]);
-                    po[2] = p[2];
-                    po[3] = p[3];
-                    if (a.flag_out) a.flag_out[f0 + fi] = static_cast<int16_t>(flag);
-                }
+            int k = threadIdx.x % T;   // (frame, tooth) of flat index i, advanced incrementally
+            for (int i = threadIdx.x; i < nf * T; i += blockDim.x) {
+                const float av = amp_s[i];
+                if (a.amps) a.amps[f0 * T + i] = av;
+                if (a.y) a.y[f0 * T + i] = av * iref[k];
+                k += blockDim.x;
+                while (k >= T) k -= T;
             }
         }
         off = offn;
@@ -198,21 +178,150 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a, FitArgs f
 }
 
 // ---------------------------------------------------------------------------
-// fit2: register-resident LM with a per-warp frame queue
+// moment initial guess, one lane per frame
 // ---------------------------------------------------------------------------
-template <int G, int PPL>
+// Comparator list of Batcher's odd-even merge sort on N = 2^m values
+// (Knuth, TAOCP vol. 3, 5.3.4), built at compile time.
+template <int N>
+struct OddEvenNet {
+    static constexpr int count_()
+    {
+        int c = 0;
+        for (int p = 1; p < N; p <<= 1)
+            for (int k = p; k >= 1; k >>= 1)
+                for (int j = k % p; j + k < N; j += 2 * k)
+                    for (int i = 0; i < k && i + j + k < N; ++i)
+                        if ((i + j) / (2 * p) == (i + j + k) / (2 * p)) ++c;
+        return c;
+    }
+    static constexpr int kCount = count_();
+    int lo[kCount], hi[kCount];
+    constexpr OddEvenNet() : lo(), hi()
+    {
+        int c = 0;
+        for (int p = 1; p < N; p <<= 1)
+            for (int k = p; k >= 1; k >>= 1)
+                for (int j = k % p; j + k < N; j += 2 * k)
+                    for (int i = 0; i < k && i + j + k < N; ++i)
+                        if ((i + j) / (2 * p) == (i + j + k) / (2 * p)) {
+                            lo[c] = i + j;
+                            hi[c] = i + j + k;
+                            ++c;
+                        }
+    }
+};
+
+// A warp stages the normalised spectra of 32 consecutive frames (row stride
+// odd, so the lanes' reads of one tooth fall on distinct banks); each lane
+// then computes its frame's guess exactly as the oracle defines it: baseline
+// = median of the outer fifth (sorted with the network, +inf padding), sign
+// of the largest deviation, centroid / extreme / area of the one-signed excess.
+template <int NPAD>
+__global__ void __launch_bounds__(128) init_kernel(InitArgs a)
+{
+    extern __shared__ __align__(16) float ism[];
+    const int T = a.T, TS = a.row_stride;
+    float* us = ism;
+    float* iref = us + T;
+    int* outer = reinterpret_cast<int*>(iref + T);
+    float* rows = reinterpret_cast<float*>(outer + a.n_outer) + (threadIdx.x >> 5) * 32 * TS;
+    for (int i = threadIdx.x; i < T; i += blockDim.x) {
+        us[i] = a.u[i];
+        iref[i] = a.inv_ref[i];
+    }
+    for (int i = threadIdx.x; i < a.n_outer; i += blockDim.x) outer[i] = a.outer_idx[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    constexpr OddEvenNet<NPAD> net{};
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t task = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+         task * 32 < a.n; task += nwarps) {
+        const int64_t f0 = task * 32;
+        const int nf = (a.n - f0) < 32 ? static_cast<int>(a.n - f0) : 32;
+        for (int f = 0; f < nf; ++f) {
+            const float* src = a.y ? a.y + (f0 + f) * T : a.amps + (f0 + f) * T;
+            for (int k = lane; k < T; k += 32) rows[f * TS + k] = a.y ? src[k] : src[k] * iref[k];
+        }
+        __syncwarp();
+        if (lane < nf) {
+            const float* r = rows + lane * TS;
+            float v[NPAD];
+#pragma unroll
+            for (int i = 0; i < NPAD; ++i) v[i] = (i < a.n_outer) ? r[outer[i]] : INFINITY;
+#pragma unroll
+            for (int c = 0; c < OddEvenNet<NPAD>::kCount; ++c) {
+                const float lo = fminf(v[net.lo[c]], v[net.hi[c]]);
+                const float hi = fmaxf(v[net.lo[c]], v[net.hi[c]]);
+                v[net.lo[c]] = lo;
+                v[net.hi[c]] = hi;
+            }
+            const int rlo = (a.n_outer - 1) >> 1, rhi = a.n_outer >> 1;
+            float vlo = 0.f, vhi = 0.f;
+#pragma unroll
+            for (int i = 0; i < NPAD; ++i) {
+                vlo = (i == rlo) ? v[i] : vlo;
+                vhi = (i == rhi) ? v[i] : vhi;
+            }
+            const float B0 = 0.5f * (vlo + vhi);
+            float best = -1.f;
+            int bestk = 0;
+            for (int k = 0; k < T; ++k) {
+                const float dv = fabsf(r[k] - B0);
+                if (dv > best) { best = dv; bestk = k; }
+            }
+            const float sgn = (r[bestk] - B0) >= 0.f ? 1.0f : -1.0f;
+            float W = 0.f, Wu = 0.f, wmax = 0.f;
+            for (int k = 0; k < T; ++k) {
+                const float w = fmaxf(sgn * (r[k] - B0), 0.f);
+                W += w;
+                Wu = fmaf(w, us[k], Wu);
+                wmax = fmaxf(wmax, w);
+            }
+            float c0, g0, A0;
+            int flag = 0;
+            if (!(W > 0.f)) {
+                c0 = a.u_mid;
+                g0 = 0.5f * a.du;
+                A0 = 0.f;
+                flag = kInitFlat;
+            } else {
+                A0 = sgn * wmax;
+                g0 = W * a.du / (3.14159265358979f * fabsf(A0));
+                g0 = fminf(fmaxf(g0, 0.5f * a.du), 0.5f * a.span);
+                c0 = Wu / W;
+            }
+            float* po = a.p0_out + (f0 + lane) * 4;
+            po[0] = fmaf(a.x_scale, c0, a.x_mid);
+            po[1] = a.x_scale * g0;
+            po[2] = A0;
+            po[3] = B0;
+            if (a.flag_out) a.flag_out[f0 + lane] = static_cast<int16_t>(flag);
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fit2: LM with each lane's spectrum points in registers and a per-warp frame
+// queue.  EXACT: PPL == ceil(T / G), so only the last point of a lane can lie
+// beyond T.
+// ---------------------------------------------------------------------------
+template <int G, int PPL, bool EXACT>
 __global__ void __launch_bounds__(256, 2) fit2_kernel(Fit2Args a)
 {
+    extern __shared__ __align__(16) float fsm[];
+    const int T = a.T;
+    float* us = fsm;
+    float* iref = fsm + T;
+    for (int i = threadIdx.x; i < T; i += blockDim.x) {
+        us[i] = a.u[i];
+        iref[i] = a.inv_ref[i];
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
     const int leader_lane = lane & ~(G - 1);
-    const int T = a.T;
-    float uv[PPL];
-#pragma unroll
-    for (int j = 0; j < PPL; ++j) {
-        const int k = gl + G * j;
-        uv[j] = (k < T) ? a.u[k] : 0.f;
-    }
+    const float inv_scale = 1.0f / a.x_scale;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
     int64_t task = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int64_t next = task * a.task;
@@ -260,15 +369,24 @@ __global__ void __launch_bounds__(256, 2) fit2_kernel(Fit2Args a)
         if (!__any_sync(kFull, f >= 0)) break;
 
         if (fresh) {
-            const float* src = a.y ? a.y + f * T : a.amps + f * T;
+            if (a.y) {
+                const float* src = a.y + f * T;
 #pragma unroll
-            for (int j = 0; j < PPL; ++j) {
-                const int k = gl + G * j;
-                yv[j] = (k < T) ? (a.y ? src[k] : src[k] * a.inv_ref[k]) : 0.f;
+                for (int j = 0; j < PPL; ++j) {
+                    const int k = gl + G * j;
+                    yv[j] = (k < T) ? src[k] : 0.f;
+                }
+            } else {
+                const float* src = a.amps + f * T;
+#pragma unroll
+                for (int j = 0; j < PPL; ++j) {
+                    const int k = gl + G * j;
+                    yv[j] = (k < T) ? src[k] * iref[k] : 0.f;
+                }
             }
             const float* q = a.p0 + f * 4;
-            p[0] = (q[0] - a.x_mid) / a.x_scale;
-            p[1] = q[1] / a.x_scale;
+            p[0] = (q[0] - a.x_mid) * inv_scale;
+            p[1] = q[1] * inv_scale;
             p[2] = q[2];
             p[3] = q[3];
             flag = a.flags_in ? (a.flags_in[f] & kInitFlat) : 0;
@@ -281,7 +399,7 @@ __global__ void __launch_bounds__(256, 2) fit2_kernel(Fit2Args a)
         bool done = false;
         if (f >= 0 && !fresh) {
             float delta[4];
-            if (lm_solve4(Nm, lambda, delta)) {
+            if (lm_solve4_fast(Nm, lambda, delta)) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) pe[i] = p[i] + delta[i];
             } else {
@@ -296,20 +414,20 @@ __global__ void __launch_bounds__(256, 2) fit2_kernel(Fit2Args a)
         const float g2 = pe[1] * pe[1];
 #pragma unroll
         for (int j = 0; j < PPL; ++j) {
-            if (gl + G * j < T) accum_point(uv[j], yv[j], pe[0], g2, pe[2], pe[3], S);
+            const int k = gl + G * j;
+            if ((EXACT && j < PPL - 1) || k < T) accum_point(us[k], yv[j], pe[0], g2, pe[2], pe[3], S);
         }
         reduce_sums<G>(S);
         // ---- LM bookkeeping ----
         if (f >= 0 && !done) {
             const float chi2t = S.v[13];
             if (fresh) {
-                fresh = false;
                 chi2 = chi2t;
                 if (!(chi2t < INFINITY)) {
                     st = kNonfinite;
                     done = true;
                 } else {
-                    make_normal(S, pe[1], pe[2], T, Nm);
+                    make_normal_fast(S, pe[1], pe[2], T, Nm);
                     if (a.max_iter <= 0) done = true;
                 }
             } else {
@@ -328,7 +446,7 @@ __global__ void __launch_bounds__(256, 2) fit2_kernel(Fit2Args a)
 #pragma unroll
                     for (int i = 0; i < 4; ++i) p[i] = pe[i];
                     chi2 = chi2t;
-                    make_normal(S, pe[1], pe[2], T, Nm);
+                    make_normal_fast(S, pe[1], pe[2], T, Nm);
                     lambda *= 0.1f;
                 } else {
                     lambda *= 10.0f;
@@ -370,66 +488,101 @@ void* fast_readout_ptr(int Q)
     }
 }
 
-template <int G, int PPL>
-static void* fit2_fn() { return reinterpret_cast<void*>(&fit2_kernel<G, PPL>); }
-
-void* fit2_ptr(int G, int PPL)
+void* init_ptr(int npad)
 {
-    switch (G * 1000 + PPL) {
-    case 4008: return fit2_fn<4, 8>();
-    case 4016: return fit2_fn<4, 16>();
-    case 4025: return fit2_fn<4, 25>();
-    case 4032: return fit2_fn<4, 32>();
-    case 8004: return fit2_fn<8, 4>();
-    case 8008: return fit2_fn<8, 8>();
-    case 8016: return fit2_fn<8, 16>();
-    case 8028: return fit2_fn<8, 28>();
-    case 8032: return fit2_fn<8, 32>();
-    case 16004: return fit2_fn<16, 4>();
-    case 16008: return fit2_fn<16, 8>();
-    case 16016: return fit2_fn<16, 16>();
-    case 32004: return fit2_fn<32, 4>();
-    case 32008: return fit2_fn<32, 8>();
+    switch (npad) {
+    case 8: return reinterpret_cast<void*>(&init_kernel<8>);
+    case 16: return reinterpret_cast<void*>(&init_kernel<16>);
+    case 32: return reinterpret_cast<void*>(&init_kernel<32>);
+    case 64: return reinterpret_cast<void*>(&init_kernel<64>);
     default: return nullptr;
     }
 }
 
-int fit2_ppl(int G, int T)
+template <int G, int PPL, bool EXACT>
+static void* fit2_fn() { return reinterpret_cast<void*>(&fit2_kernel<G, PPL, EXACT>); }
+
+// Instantiated (G, PPL): exact fits for the workload geometries
+// (T = 21, 99 with G = 4; T = 201, 221 with G = 8; T = 21, 99, 201, 221 with
+// G = 16, 32) and a general ladder with full tail checks.
+struct Fit2Inst {
+    int G, PPL;
+    bool exact;
+    void* (*fn)();
+};
+static const Fit2Inst kFit2[] = {
+    {4, 6, true, fit2_fn<4, 6, true>},     {4, 25, true, fit2_fn<4, 25, true>},
+    {8, 26, true, fit2_fn<8, 26, true>},   {8, 28, true, fit2_fn<8, 28, true>},
+    {8, 3, true, fit2_fn<8, 3, true>},     {8, 13, true, fit2_fn<8, 13, true>},
+    {16, 2, true, fit2_fn<16, 2, true>},   {16, 7, true, fit2_fn<16, 7, true>},
+    {16, 13, true, fit2_fn<16, 13, true>}, {16, 14, true, fit2_fn<16, 14, true>},
+    {32, 1, true, fit2_fn<32, 1, true>},   {32, 4, true, fit2_fn<32, 4, true>},
+    {32, 7, true, fit2_fn<32, 7, true>},
+    {4, 8, false, fit2_fn<4, 8, false>},   {4, 16, false, fit2_fn<4, 16, false>},
+    {4, 32, false, fit2_fn<4, 32, false>}, {8, 8, false, fit2_fn<8, 8, false>},
+    {8, 16, false, fit2_fn<8, 16, false>}, {8, 32, false, fit2_fn<8, 32, false>},
+    {16, 8, false, fit2_fn<16, 8, false>}, {16, 16, false, fit2_fn<16, 16, false>},
+    {32, 8, false, fit2_fn<32, 8, false>},
+};
+
+void* fit2_ptr(int G, int PPL, bool exact)
 {
-    static const int kG4[] = {8, 16, 25, 32};
-    static const int kG8[] = {4, 8, 16, 28, 32};
-    static const int kG16[] = {4, 8, 16};
-    static const int kG32[] = {4, 8};
+    for (const Fit2Inst& f : kFit2)
+        if (f.G == G && f.PPL == PPL && f.exact == exact) return f.fn();
+    return nullptr;
+}
+
+// smallest instantiated PPL for (G, T); *exact tells whether it is ceil(T/G)
+int fit2_ppl(int G, int T, bool* exact)
+{
     const int need = (T + G - 1) / G;
-    const int* list = nullptr;
-    int cnt = 0;
-    switch (G) {
-    case 4: list = kG4; cnt = 4; break;
-    case 8: list = kG8; cnt = 5; break;
-    case 16: list = kG16; cnt = 3; break;
-    case 32: list = kG32; cnt = 2; break;
-    default: return 0;
-    }
-    for (int i = 0; i < cnt; ++i)
-        if (list[i] >= need) return list[i];
+    for (const Fit2Inst& f : kFit2)
+        if (f.G == G && f.exact && f.PPL == need) {
+            *exact = true;
+            return need;
+        }
+    int best = 0;
+    for (const Fit2Inst& f : kFit2)
+        if (f.G == G && !f.exact && f.PPL >= need && (best == 0 || f.PPL < best)) best = f.PPL;
+    *exact = false;
+    return best;
+}
+
+int init_npad(int n_outer)
+{
+    for (int np : {8, 16, 32, 64})
+        if (n_outer <= np) return np;
     return 0;
 }
 
 cudaError_t launch_fast_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps,
-                                float* y, float* p0_out, int16_t* flag_out, cudaStream_t s)
+                                float* y, cudaStream_t s)
 {
     FastArgs a = p->fa;
     a.frames = frames;
     a.n_frames = n;
     a.amps = amps;
     a.y = y;
-    a.p0_out = p0_out;
-    a.flag_out = flag_out;
-    FitArgs fa = make_fit_args(p);
     const int64_t nb = (n + a.F - 1) / a.F;
     const int grid = static_cast<int>(nb < p->grid_fast ? nb : p->grid_fast);
-    void* args[] = {&a, &fa};
+    void* args[] = {&a};
     return cudaLaunchKernel(fast_readout_ptr(p->Q), dim3(grid), dim3(128), args, a.sm_total, s);
+}
+
+cudaError_t launch_init(const cg_plan_s* p, const float* y, const float* amps, int64_t n,
+                        float* p0_out, int16_t* flag_out, cudaStream_t s)
+{
+    InitArgs a = p->ia;
+    a.n = n;
+    a.y = y;
+    a.amps = amps;
+    a.p0_out = p0_out;
+    a.flag_out = flag_out;
+    const int64_t tasks = (n + 31) / 32;
+    const int64_t blocks = (tasks + 3) / 4;
+    const int grid = static_cast<int>(blocks < p->grid_init ? blocks : p->grid_init);
+    void* args[] = {&a};
+    return cudaLaunchKernel(init_ptr(p->init_npad), dim3(grid), dim3(128), args, p->init_smem, s);
 }
 
 cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, int64_t n,
@@ -464,7 +617,8 @@ cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, i
     const int64_t blocks = (tasks + 7) / 8;
     const int grid = static_cast<int>(blocks < p->grid_fit2 ? blocks : p->grid_fit2);
     void* args[] = {&a};
-    return cudaLaunchKernel(fit2_ptr(p->G2, p->PPL), dim3(grid), dim3(256), args, 0, s);
+    return cudaLaunchKernel(fit2_ptr(p->G2, p->PPL, p->ppl_exact), dim3(grid), dim3(256), args,
+                            8 * p->T, s);
 }
 
 }  // namespace cg

@@ -231,6 +231,78 @@ __device__ __forceinline__ bool lm_solve4(const Normal& N, float lambda, float (
     return true;
 }
 
+// --- throughput variants: approximate reciprocal / reciprocal square root ---
+// (the step only has to point downhill; the fixed point is set by the sums)
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void make_normal_fast(const LmSums& S, float g, float A, int T, Normal& N)
+{
+    const float ac = 2.0f * A;
+    const float ag = ac * rcp_approx(g);
+    N.H[0] = ac * ac * S.v[4];
+    N.H[1] = ac * ag * S.v[5];
+    N.H[2] = ac * S.v[1];
+    N.H[3] = ac * S.v[6];
+    N.H[4] = ag * ag * S.v[7];
+    N.H[5] = ag * S.v[2];
+    N.H[6] = ag * S.v[8];
+    N.H[7] = S.v[0];
+    N.H[8] = S.v[3];
+    N.H[9] = static_cast<float>(T);
+    N.b[0] = ac * S.v[10];
+    N.b[1] = ag * S.v[11];
+    N.b[2] = S.v[9];
+    N.b[3] = S.v[12];
+}
+
+// Cholesky of S H S + lambda I keeping only the inverse pivots (rsqrt).
+__device__ __forceinline__ bool lm_solve4_fast(const Normal& N, float lambda, float (&delta)[4])
+{
+    const float dH[4] = {N.H[0], N.H[4], N.H[7], N.H[9]};
+    float s[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (!(dH[i] > 0.0f) || !(dH[i] < INFINITY)) return false;
+        s[i] = rsqrtf(dH[i]);
+    }
+    const float dg = 1.0f + lambda;
+    const float m10 = N.H[1] * s[1] * s[0];
+    const float m20 = N.H[2] * s[2] * s[0], m21 = N.H[5] * s[2] * s[1];
+    const float m30 = N.H[3] * s[3] * s[0], m31 = N.H[6] * s[3] * s[1], m32 = N.H[8] * s[3] * s[2];
+    const float i00 = rsqrtf(dg);
+    const float l10 = m10 * i00, l20 = m20 * i00, l30 = m30 * i00;
+    const float v11 = fmaf(-l10, l10, dg);
+    if (!(v11 > 0.f)) return false;
+    const float i11 = rsqrtf(v11);
+    const float l21 = fmaf(-l20, l10, m21) * i11;
+    const float l31 = fmaf(-l30, l10, m31) * i11;
+    const float v22 = fmaf(-l21, l21, fmaf(-l20, l20, dg));
+    if (!(v22 > 0.f)) return false;
+    const float i22 = rsqrtf(v22);
+    const float l32 = fmaf(-l31, l21, fmaf(-l30, l20, m32)) * i22;
+    const float v33 = fmaf(-l32, l32, fmaf(-l31, l31, fmaf(-l30, l30, dg)));
+    if (!(v33 > 0.f)) return false;
+    const float i33 = rsqrtf(v33);
+    const float z0 = N.b[0] * s[0] * i00;
+    const float z1 = fmaf(-l10, z0, N.b[1] * s[1]) * i11;
+    const float z2 = fmaf(-l21, z1, fmaf(-l20, z0, N.b[2] * s[2])) * i22;
+    const float z3 = fmaf(-l32, z2, fmaf(-l31, z1, fmaf(-l30, z0, N.b[3] * s[3]))) * i33;
+    const float u3 = z3 * i33;
+    const float u2 = fmaf(-l32, u3, z2) * i22;
+    const float u1 = fmaf(-l31, u3, fmaf(-l21, u2, z1)) * i11;
+    const float u0 = fmaf(-l30, u3, fmaf(-l20, u2, fmaf(-l10, u1, z0))) * i00;
+    delta[0] = u0 * s[0];
+    delta[1] = u1 * s[1];
+    delta[2] = u2 * s[2];
+    delta[3] = u3 * s[3];
+    return true;
+}
+
 // Moment initial guess on the normalised abscissa (see the oracle for the
 // reading): baseline = median of the outer fifth, centroid of the one-signed
 // excess, amplitude = its extreme, width from area / (pi |A|).

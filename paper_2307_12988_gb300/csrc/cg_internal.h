@@ -61,6 +61,22 @@ struct FastArgs {
     int sm_twL, sm_twN, sm_tom, sm_iref, sm_u, sm_raw, sm_Y, sm_amps, sm_y, sm_total;
 };
 
+// Arguments of the lane-per-frame moment initial guess.
+struct InitArgs {
+    int64_t n;
+    int T;
+    int row_stride;          // odd row stride of the staged spectra
+    int n_outer;
+    const float* y;          // [n][T] normalised, or null
+    const float* amps;       // [n][T] magnitudes when y is null
+    const float* inv_ref;    // [T]
+    const float* u;          // [T]
+    const int* outer_idx;    // [n_outer]
+    float u_mid, du, span, x_mid, x_scale;
+    float* p0_out;           // [n][4] abscissa units
+    int16_t* flag_out;       // [n] or null
+};
+
 // Arguments of the register-resident LM kernel.
 struct Fit2Args {
     int64_t n;
@@ -123,7 +139,10 @@ struct cg_plan_s {
     int Q = 0;               // L = 10 Q
     int G2 = 4;              // LM lanes per frame of the register-resident fit
     int PPL = 0;             // LM points per lane
-    int grid_fast = 0, grid_fit2 = 0;
+    bool ppl_exact = false;  // PPL == ceil(T / G2)
+    int grid_fast = 0, grid_fit2 = 0, grid_init = 0;
+    int init_npad = 0, init_smem = 0;
+    cg::InitArgs ia{};
     int64_t chunk = 0;       // frames per pipelined chunk
     cg::FastArgs fa{};
     cudaStream_t s_read = nullptr, s_fit = nullptr;
@@ -152,10 +171,14 @@ FitArgs make_fit_args(const cg_plan_s* p);
 
 // throughput path (cg_fast.cu)
 void* fast_readout_ptr(int Q);
-void* fit2_ptr(int G, int PPL);
-int fit2_ppl(int G, int T);
+void* init_ptr(int npad);
+int init_npad(int n_outer);
+void* fit2_ptr(int G, int PPL, bool exact);
+int fit2_ppl(int G, int T, bool* exact);
 cudaError_t launch_fast_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps,
-                                float* y, float* p0_out, int16_t* flag_out, cudaStream_t s);
+                                float* y, cudaStream_t s);
+cudaError_t launch_init(const cg_plan_s* p, const float* y, const float* amps, int64_t n,
+                        float* p0_out, int16_t* flag_out, cudaStream_t s);
 cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, int64_t n,
                         const float* p0, const int16_t* flags_in, float* params, float* rss,
                         int16_t* iters, int16_t* status, cudaStream_t s);
