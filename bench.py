@@ -151,9 +151,9 @@ def cpu_baseline_leg(frames, params, status, iters, plan, ref, g, args) -> dict:
 def launches_per_step(plan, n) -> int:
     """Kernels of this library that one cg_process call launches."""
     path = plan.info["path"]
-    if path == 3:   # pipeline: a readout and a fit kernel per chunk
-        chunk = plan._opts.chunk_frames or 65536
-        return 2 * ((n + chunk - 1) // chunk)
+    if path == 3:   # pipeline: readout, initial guess and fit kernels per chunk
+        chunk = plan._opts.chunk_frames or n
+        return 3 * ((n + chunk - 1) // chunk)
     return 1 if path == 1 else 2
 
 

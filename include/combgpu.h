@@ -83,7 +83,7 @@ typedef struct cg_opts {
     int lanes_per_frame;  /* LM lanes cooperating on one frame: 4, 8, 16 or 32
                              (32 = one warp per frame); 0 = library default */
     int path;             /* CG_PATH_* (default CG_PATH_AUTO) */
-    int chunk_frames;     /* frames per pipelined chunk; 0 = 65536 */
+    int chunk_frames;     /* frames per pipelined chunk; 0 = the whole call */
     int reserved[7];      /* must be zero */
 } cg_opts;
 

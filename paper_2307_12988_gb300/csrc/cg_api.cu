@@ -118,6 +118,7 @@ void free_tables(cg::DevTables& d)
     cudaFree(d.ref_out);
     cudaFree(d.tw_M5);
     cudaFree(d.tooth_of_m);
+    cudaFree(d.fit_counter);
     d = cg::DevTables{};
 }
 
@@ -146,8 +147,9 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
         if (tom[zidx[k]] >= 0) return cudaSuccess;   // two teeth on one bin: generic path
         tom[zidx[k]] = k;
     }
-    // LM lanes per frame: 4 unless a lane would hold more than 28 points
-    int G = p->opts.lanes_per_frame ? p->opts.lanes_per_frame : (T <= 112 ? 4 : 8);
+    // LM lanes per frame: one lane per frame while the spectrum fits in its
+    // registers (T <= 100), else 4 or 8 lanes with shuffle reductions
+    int G = p->opts.lanes_per_frame ? p->opts.lanes_per_frame : (T <= 100 ? 1 : (T <= 112 ? 4 : 8));
     bool exact = false;
     int ppl = cg::fit2_ppl(G, T, &exact);
     while (ppl == 0 && G < 32 && !p->opts.lanes_per_frame) ppl = cg::fit2_ppl(G *= 2, T, &exact);
@@ -158,9 +160,10 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
     // (stage 1: 10 items per frame, cost ~ 50 Q; stage 2: Q items, cost ~ 200)
     int bestF = 2;
     double best = 1e30;
+    // (at most ~52 KiB of shared memory per block keeps four blocks per SM)
     for (int F = 2; F <= 32; ++F) {
         const int bytes = 2 * N * F + 32 + 8 * L * F + 4 * T * F;
-        if (bytes > 96 * 1024) break;
+        if (bytes > 52 * 1024) break;
         const double cost = (std::ceil(10.0 * F / 128.0) * 50.0 * Q + std::ceil(double(Q) * F / 128.0) * 200.0) / F;
         if (cost < best - 1e-9) { best = cost; bestF = F; }
     }
@@ -216,7 +219,10 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
     if (occ < 1) return cudaSuccess;
     p->grid_fast = p->num_sms * occ;
     void* ff = cg::fit2_ptr(G, ppl, exact);
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ff, 256, 8 * T)) != cudaSuccess) return e;
+    const size_t fsm = cg::fit2_smem(G, T);
+    if ((e = cudaFuncSetAttribute(ff, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(fsm))) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ff, cg::fit2_threads(G), fsm)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&p->d.fit_counter, sizeof(unsigned long long))) != cudaSuccess) return e;
     if (occ < 1) return cudaSuccess;
     p->grid_fit2 = p->num_sms * occ;
     void* fi = cg::init_ptr(npad);
@@ -232,7 +238,9 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
     p->Q = Q;
     p->G2 = G;
     p->PPL = ppl;
-    p->chunk = p->opts.chunk_frames ? p->opts.chunk_frames : 65536;
+    // 0: the whole call is one chunk (one launch per kernel; measured fastest
+    // for large calls, since each kernel then has frames enough for every SM)
+    p->chunk = p->opts.chunk_frames ? p->opts.chunk_frames : (int64_t(1) << 40);
     p->fast_ok = true;
     return cudaSuccess;
 }
@@ -301,9 +309,10 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
     if (opts) o = *opts;
     if (o.max_iter < 0 || o.max_iter > 32767) return fail(CG_ERR_ARG, "max_iter outside [0, 32767]");
     if (!(o.tol >= 0.0) || !(o.lambda0 > 0.0)) return fail(CG_ERR_ARG, "tol must be >= 0 and lambda0 > 0");
-    if (o.lanes_per_frame != 0 && o.lanes_per_frame != 4 && o.lanes_per_frame != 8 &&
-        o.lanes_per_frame != 16 && o.lanes_per_frame != 32)
-        return fail(CG_ERR_ARG, "lanes_per_frame must be 0, 4, 8, 16 or 32");
+    if (o.lanes_per_frame != 0 && o.lanes_per_frame != 1 && o.lanes_per_frame != 2 &&
+        o.lanes_per_frame != 4 && o.lanes_per_frame != 8 && o.lanes_per_frame != 16 &&
+        o.lanes_per_frame != 32)
+        return fail(CG_ERR_ARG, "lanes_per_frame must be 0, 1, 2, 4, 8, 16 or 32");
     if (o.path < CG_PATH_AUTO || o.path > CG_PATH_PIPELINE) return fail(CG_ERR_ARG, "path must be a CG_PATH_* value");
     if (o.chunk_frames < 0) return fail(CG_ERR_ARG, "chunk_frames must be >= 0");
     if (o.readout != CG_READOUT_FFT) return fail(CG_ERR_UNSUPPORTED, "readout kind %d not available", o.readout);
@@ -375,7 +384,9 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         delete p;
         return fail(CG_ERR_UNSUPPORTED, "frame_len %d: transform length is not a product of 2,3,5,7,11,13", N);
     }
-    p->G = o.lanes_per_frame ? o.lanes_per_frame : 8;
+    // the fused / split kernels take groups of 4..32 lanes (1 and 2 exist only
+    // in the pipelined fit)
+    p->G = o.lanes_per_frame >= 4 ? o.lanes_per_frame : 8;
 
     // twiddles (FP64 on the host, rounded to FP32)
     const int L = p->L, M = p->M;

@@ -238,9 +238,31 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
          task * 32 < a.n; task += nwarps) {
         const int64_t f0 = task * 32;
         const int nf = (a.n - f0) < 32 ? static_cast<int>(a.n - f0) : 32;
-        for (int f = 0; f < nf; ++f) {
-            const float* src = a.y ? a.y + (f0 + f) * T : a.amps + (f0 + f) * T;
-            for (int k = lane; k < T; k += 32) rows[f * TS + k] = a.y ? src[k] : src[k] * iref[k];
+        // the 32 rows are contiguous in global memory: one flat coalesced
+        // sweep, eight loads in flight per lane, (frame, tooth) tracked
+        // incrementally
+        {
+            const float* src = (a.y ? a.y : a.amps) + f0 * T;
+            const int total = nf * T;
+            int f = lane / T, k = lane - (lane / T) * T;
+            for (int e0 = 0; e0 < total; e0 += 8 * 32) {
+                float v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int e = e0 + q * 32 + lane;
+                    v[q] = e < total ? src[e] : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int e = e0 + q * 32 + lane;
+                    if (e < total) rows[f * TS + k] = a.y ? v[q] : v[q] * iref[k];
+                    k += 32;
+                    while (k >= T) {
+                        k -= T;
+                        ++f;
+                    }
+                }
+            }
         }
         __syncwarp();
         if (lane < nf) {
@@ -307,7 +329,7 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
 // beyond T.
 // ---------------------------------------------------------------------------
 template <int G, int PPL, bool EXACT>
-__global__ void __launch_bounds__(256, 2) fit2_kernel(Fit2Args a)
+__global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kernel(Fit2Args a)
 {
     extern __shared__ __align__(16) float fsm[];
     const int T = a.T;
@@ -322,11 +344,7 @@ __global__ void __launch_bounds__(256, 2) fit2_kernel(Fit2Args a)
     const int gl = lane & (G - 1);
     const int leader_lane = lane & ~(G - 1);
     const float inv_scale = 1.0f / a.x_scale;
-    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-    int64_t task = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int64_t next = task * a.task;
-    int64_t end = next + a.task < a.n ? next + a.task : a.n;
-    if (next >= a.n) next = end = a.n;
+    int64_t next = 0, end = 0;   // current task [next, end); tasks come from a.counter
 
     int64_t f = -1;
     float yv[PPL];
@@ -347,8 +365,10 @@ __global__ void __launch_bounds__(256, 2) fit2_kernel(Fit2Args a)
         unsigned need = __ballot_sync(kFull, gl == 0 && f < 0);
         while (need != 0 && next < a.n) {
             if (next >= end) {
-                task += nwarps;
-                next = task * a.task;
+                unsigned long long t = 0;
+                if (lane == 0) t = atomicAdd(a.counter, 1ULL);
+                t = __shfl_sync(kFull, t, 0);
+                next = static_cast<int64_t>(t) * a.task;
                 if (next >= a.n) {
                     next = end = a.n;
                     break;
@@ -417,7 +437,7 @@ __global__ void __launch_bounds__(256, 2) fit2_kernel(Fit2Args a)
             const int k = gl + G * j;
             if ((EXACT && j < PPL - 1) || k < T) accum_point(us[k], yv[j], pe[0], g2, pe[2], pe[3], S);
         }
-        reduce_sums<G>(S);
+        if constexpr (G > 1) reduce_sums<G>(S);
         // ---- LM bookkeeping ----
         if (f >= 0 && !done) {
             const float chi2t = S.v[13];
@@ -511,6 +531,7 @@ struct Fit2Inst {
     void* (*fn)();
 };
 static const Fit2Inst kFit2[] = {
+    {2, 50, true, fit2_fn<2, 50, true>},   {2, 11, true, fit2_fn<2, 11, true>},
     {4, 6, true, fit2_fn<4, 6, true>},     {4, 25, true, fit2_fn<4, 25, true>},
     {8, 26, true, fit2_fn<8, 26, true>},   {8, 28, true, fit2_fn<8, 28, true>},
     {8, 3, true, fit2_fn<8, 3, true>},     {8, 13, true, fit2_fn<8, 13, true>},
@@ -527,6 +548,7 @@ static const Fit2Inst kFit2[] = {
 
 void* fit2_ptr(int G, int PPL, bool exact)
 {
+    if (G == 1) return fit1_ptr();
     for (const Fit2Inst& f : kFit2)
         if (f.G == G && f.PPL == PPL && f.exact == exact) return f.fn();
     return nullptr;
@@ -535,6 +557,10 @@ void* fit2_ptr(int G, int PPL, bool exact)
 // smallest instantiated PPL for (G, T); *exact tells whether it is ceil(T/G)
 int fit2_ppl(int G, int T, bool* exact)
 {
+    if (G == 1) {   // the lane-per-frame kernel keeps spectra in shared memory
+        *exact = true;
+        return T;
+    }
     const int need = (T + G - 1) / G;
     for (const Fit2Inst& f : kFit2)
         if (f.G == G && f.exact && f.PPL == need) {
@@ -547,6 +573,9 @@ int fit2_ppl(int G, int T, bool* exact)
     *exact = false;
     return best;
 }
+
+int fit2_threads(int G) { return G == 1 ? 128 : 256; }
+size_t fit2_smem(int G, int T);
 
 int init_npad(int n_outer)
 {
@@ -607,18 +636,28 @@ cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, i
     a.rss = rss;
     a.iters = iters;
     a.status = status;
-    const int warps_total = p->grid_fit2 * 8;
-    const int gpw = 32 / p->G2;  // groups per warp
-    int64_t per = (n + warps_total - 1) / warps_total;
-    if (per < 2 * gpw) per = 2 * gpw;
-    per = ((per + gpw - 1) / gpw) * gpw;
-    a.task = static_cast<int>(per);
-    const int64_t tasks = (n + per - 1) / per;
-    const int64_t blocks = (tasks + 7) / 8;
+    a.row_stride = p->T | 1;
+    a.counter = p->d.fit_counter;
+    // tasks are claimed dynamically: a few frames per lane group per task
+    const int gpw = 32 / p->G2;                   // groups per warp
+    a.task = 2 * gpw;
+    const int threads = fit2_threads(p->G2);
+    const int wpb = threads / 32;                 // warps per block
+    const int64_t tasks = (n + a.task - 1) / a.task;
+    const int64_t blocks = (tasks + wpb - 1) / wpb;
     const int grid = static_cast<int>(blocks < p->grid_fit2 ? blocks : p->grid_fit2);
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
     void* args[] = {&a};
-    return cudaLaunchKernel(fit2_ptr(p->G2, p->PPL, p->ppl_exact), dim3(grid), dim3(256), args,
-                            8 * p->T, s);
+    return cudaLaunchKernel(fit2_ptr(p->G2, p->PPL, p->ppl_exact), dim3(grid), dim3(threads), args,
+                            fit2_smem(p->G2, p->T), s);
+}
+
+size_t fit2_smem(int G, int T)
+{
+    // G == 1: abscissa table, 4 warps x [2][32] row slots, 4 x 32 slot offsets
+    return G == 1 ? sizeof(float) * (T + 4 * 64 * (T | 1)) + sizeof(int) * 4 * 32
+                  : sizeof(float) * 2 * T;
 }
 
 }  // namespace cg

@@ -126,12 +126,19 @@ __device__ __forceinline__ void reduce_sums(LmSums& S)
         S.v[idx] = __shfl_sync(kFull, a[red_slot(idx, G)], gbase + red_owner(idx, G));
 }
 
+__device__ __forceinline__ float rcp_fast(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ void accum_point(float u, float y, float c, float g2, float A, float B,
                                             LmSums& S)
 {
     const float d = u - c;
     const float D = fmaf(d, d, g2);
-    const float q = __fdividef(1.0f, D);
+    const float q = rcp_fast(D);
     const float L = g2 * q;
     const float r = y - fmaf(A, L, B);
     const float t = L * q;

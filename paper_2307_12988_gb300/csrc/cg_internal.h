@@ -82,6 +82,8 @@ struct Fit2Args {
     int64_t n;
     int T;
     int task;                // frames per warp task
+    int row_stride;          // odd stride of the lane-per-frame spectrum slots
+    unsigned long long* counter;  // next task (zeroed before the launch)
     const float* y;          // [n][T] normalised, or null
     const float* amps;       // [n][T] magnitudes when y is null
     const float* inv_ref;    // [T]
@@ -111,6 +113,7 @@ struct DevTables {
     double* ref_part = nullptr;   // [ref_part_rows][T]
     double* ref_out = nullptr;    // [T]
     int ref_part_rows = 0;
+    unsigned long long* fit_counter = nullptr;   // dynamic task counter of the fit kernels
 };
 
 }  // namespace cg
@@ -175,6 +178,9 @@ void* init_ptr(int npad);
 int init_npad(int n_outer);
 void* fit2_ptr(int G, int PPL, bool exact);
 int fit2_ppl(int G, int T, bool* exact);
+int fit2_threads(int G);
+void* fit1_ptr();   // lane-per-frame LM kernel (cg_fit1.cu)
+size_t fit2_smem(int G, int T);
 cudaError_t launch_fast_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps,
                                 float* y, cudaStream_t s);
 cudaError_t launch_init(const cg_plan_s* p, const float* y, const float* amps, int64_t n,

@@ -55,6 +55,7 @@ def test_defaults():
     (dict(ref=np.array([1.0, 1.0, 0.0, 1.0, 1.0])), "ref_spectrum"),
     (dict(tooth_freqs=np.array([1e6, np.nan, 3e6, 4e6, 5e6])), "tooth_freqs"),
     (dict(opts=dict(lanes_per_frame=5)), "lanes_per_frame"),
+    (dict(opts=dict(lanes_per_frame=3)), "lanes_per_frame"),
     (dict(opts=dict(max_iter=-1)), "max_iter"),
 ])
 def test_plan_argument_errors_before_cuda(kw, err):
