@@ -104,12 +104,34 @@ def _dist():
     return ws, rank, local
 
 
-def build_workload(n_frames, n_ref, device, seed_offset=0):
+GEOMETRIES = {
+    # name: (synth geometry attribute, generator keywords)
+    "paper_rate": ("PAPER_RATE", dict(snr_db=30.0, center_amp_hz=20e6)),
+    "wide": ("WIDE", dict(snr_db=30.0, center_amp_hz=20e6)),
+    "tiny": ("TINY", dict(sigma=0.01 * 2048, center_amp_hz=5e6)),
+    "serve4096": ("SERVE_4096", dict(snr_db=30.0, center_amp_hz=20e6)),
+}
+
+
+def workload_name(args, n):
+    g = geometry(args)
+    return (f"{args.workload}_{g.sample_rate / 1e9:g}GSps_N{g.frame_len}_T{g.n_teeth}_"
+            f"{n}frames_{args.readout}")
+
+
+def geometry(args):
     import synth
-    g = synth.PAPER_RATE
+    return getattr(synth, GEOMETRIES[args.workload][0])
+
+
+def build_workload(args, n_frames, n_ref, device, seed_offset=0):
+    import synth
+    g = geometry(args)
+    kw = GEOMETRIES[args.workload][1]
     stream = synth.make_stream(g, synth.BASE_SEED + 2 + seed_offset)
-    fr = synth.frames(stream, n_frames, snr_db=30.0, center_amp_hz=20e6, device=device)
-    rf = synth.frames(stream, n_ref, cavity=False, snr_db=30.0, noise_stream=1, device=device)
+    fr = synth.frames(stream, n_frames, device=device, **kw)
+    noise = {k: v for k, v in kw.items() if k in ("snr_db", "sigma")}
+    rf = synth.frames(stream, n_ref, cavity=False, noise_stream=1, device=device, **noise)
     return g, fr["frames"], rf["frames"]
 
 
@@ -132,7 +154,7 @@ def cpu_baseline_leg(frames, params, status, iters, plan, ref, g, args) -> dict:
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     cpu = {"value": n / dt, "unit": "spectra/s", "cores": cores, "kind": "oracle",
            "sample": f"first {n} of the workload's frames (FP64 direct-sum DFT at the "
-                     f"99 teeth, moment init, 20-iteration LM), {dt:.1f} s"}
+                     f"{g.n_teeth} teeth, moment init, 20-iteration LM), {dt:.1f} s"}
     rng = np.random.default_rng(7)
     idx = np.sort(rng.choice(frames_host.shape[0], size=min(256, frames_host.shape[0]),
                              replace=False))
@@ -168,13 +190,15 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = args.frames
-    g, frames, ref_frames = build_workload(n, args.ref_frames, dev, seed_offset=rank)
+    g, frames, ref_frames = build_workload(args, n, args.ref_frames, dev, seed_offset=rank)
     plan0 = cg.Plan(g.sample_rate, g.frame_len, g.tooth_freqs, g.tooth_x)
     ref = plan0.reference_accumulate(ref_frames)
     plan0.close()
     del ref_frames
     plan = cg.Plan(g.sample_rate, g.frame_len, g.tooth_freqs, g.tooth_x, ref,
-                   lanes_per_frame=args.lanes, path=args.path, chunk_frames=args.chunk)
+                   lanes_per_frame=args.lanes, path=args.path, chunk_frames=args.chunk,
+                   readout=(cg.READOUT_GEMM_SPLIT if args.readout == "gemm" else cg.READOUT_FFT),
+                   sample_bits=args.sample_bits)
     T = plan.T
     amps = torch.empty((n, T), dtype=torch.float32, device=dev)
     params = torch.empty((n, 4), dtype=torch.float32, device=dev)
@@ -222,7 +246,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded comb interferograms, 12-bit in int16)",
-        "config": {"workload": "paper_rate_1.1GSps_N1100_T99_1e6frames",
+        "config": {"workload": workload_name(args, n),
                    "frames_per_gpu": n, "frame_len": g.frame_len, "teeth": T,
                    "sample_rate_hz": g.sample_rate, "resident_bytes": 2 * g.frame_len * n,
                    "l2": "inputs (2.2 GB) larger than L2; no flush",
@@ -356,6 +380,10 @@ def main():
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--path", type=int, default=0, help="0 auto, 1 fused, 2 split, 3 pipeline")
     ap.add_argument("--chunk", type=int, default=0, help="frames per pipelined chunk (0: default)")
+    ap.add_argument("--workload", choices=sorted(GEOMETRIES), default="paper_rate")
+    ap.add_argument("--readout", choices=["fft", "gemm"], default="fft")
+    ap.add_argument("--sample-bits", type=int, default=12,
+                    help="declared sample range for the GEMM readout (the workloads are 12-bit)")
     ap.add_argument("--quick", action="store_true", help="skip fit check, CPU baseline and e2e")
     ap.add_argument("--check-frames", type=int, default=200_000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -84,7 +84,12 @@ typedef struct cg_opts {
                              (32 = one warp per frame); 0 = library default */
     int path;             /* CG_PATH_* (default CG_PATH_AUTO) */
     int chunk_frames;     /* frames per pipelined chunk; 0 = the whole call */
-    int reserved[7];      /* must be zero */
+    int sample_bits;      /* GEMM readout: 12 = samples lie in [-2048, 2047] and are
+                             exact in FP16 (two products per step); 16 (default) =
+                             full int16, split into 256 hi + lo (four products) */
+    int solve_f64;        /* -1 (default): FP64 4x4 LM solve with the GEMM readout,
+                             FP32 otherwise; 0: FP32; 1: FP64 */
+    int reserved[5];      /* must be zero */
 } cg_opts;
 
 typedef struct cg_plan_s* cg_plan_t;
@@ -210,6 +215,15 @@ cg_status cg_reference_accumulate(cg_plan_t plan, const int16_t* frames_dev, int
  */
 cg_status cg_reference_accumulate_noalloc(cg_plan_t plan, const int16_t* frames_dev,
                                           int64_t n, double* ref_dev, void* cuda_stream);
+
+/*
+ * cg_check_device -- synchronise the plan's device and report (then clear)
+ * the plan's device-side error word.  Kernels never trap: a kernel whose
+ * bounded wait on a pipeline barrier runs out records the event there,
+ * unwinds and leaves its outputs unwritten.  Returns CG_OK or
+ * CG_ERR_DEVICE_CHECK (or CG_ERR_CUDA if the synchronisation fails).
+ */
+cg_status cg_check_device(cg_plan_t plan);
 
 /* Text of a status code (static storage). */
 const char* cg_status_string(cg_status status);

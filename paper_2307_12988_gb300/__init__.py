@@ -11,7 +11,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import _binding
-from ._binding import (CgError, cg_fit, cg_opts_default, cg_plan, cg_plan_describe,
+from ._binding import (CgError, cg_check_device, cg_fit, cg_opts_default, cg_plan, cg_plan_describe,
                        cg_plan_destroy, cg_process, cg_readout, cg_reference_accumulate,
                        cg_set_reference, cg_status_string, cg_version, load)
 from ._binding import (FFT_AUTO, FFT_COSET, FFT_FULL, FIT_CONVERGED, FIT_INIT_FLAT,

@@ -43,7 +43,8 @@ class cg_opts(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
                 ("lambda0", ctypes.c_double), ("lanes_per_frame", ctypes.c_int),
                 ("path", ctypes.c_int), ("chunk_frames", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("sample_bits", ctypes.c_int), ("solve_f64", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class cg_plan_info(ctypes.Structure):
@@ -68,6 +69,7 @@ _SIGS = {
     "cg_fit": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
     "cg_reference_accumulate": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     "cg_reference_accumulate_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    "cg_check_device": (ctypes.c_int, [_P]),
     "cg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cg_last_error": (ctypes.c_char_p, []),
     "cg_version": (ctypes.c_int, []),
@@ -213,6 +215,11 @@ def cg_reference_accumulate_noalloc(plan: int, frames, n: int, ref_dev, stream=N
     _check(load().cg_reference_accumulate_noalloc(plan, _ptr(frames), int(n), _ptr(ref_dev),
                                                   _stream(stream)),
            "cg_reference_accumulate_noalloc")
+
+
+def cg_check_device(plan: int) -> None:
+    """Synchronise and raise CgError if a kernel recorded a device-side error."""
+    _check(load().cg_check_device(plan), "cg_check_device")
 
 
 def cg_status_string(status: int) -> str:

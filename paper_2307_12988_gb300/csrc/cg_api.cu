@@ -119,6 +119,8 @@ void free_tables(cg::DevTables& d)
     cudaFree(d.tw_M5);
     cudaFree(d.tooth_of_m);
     cudaFree(d.fit_counter);
+    cudaFree(d.gemm_W);
+    cudaFree(d.err);
     d = cg::DevTables{};
 }
 
@@ -147,15 +149,7 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
         if (tom[zidx[k]] >= 0) return cudaSuccess;   // two teeth on one bin: generic path
         tom[zidx[k]] = k;
     }
-    // LM lanes per frame: one lane per frame while the spectrum fits in its
-    // registers (T <= 100), else 4 or 8 lanes with shuffle reductions
-    int G = p->opts.lanes_per_frame ? p->opts.lanes_per_frame : (T <= 100 ? 1 : (T <= 112 ? 4 : 8));
-    bool exact = false;
-    int ppl = cg::fit2_ppl(G, T, &exact);
-    while (ppl == 0 && G < 32 && !p->opts.lanes_per_frame) ppl = cg::fit2_ppl(G *= 2, T, &exact);
-    if (ppl == 0) return cudaSuccess;
-    const int npad = cg::init_npad(p->n_outer);
-    if (npad == 0) return cudaSuccess;
+    if (!p->fit_ok) return cudaSuccess;
     // batch size: minimise idle thread slots of the two transform stages
     // (stage 1: 10 items per frame, cost ~ 50 Q; stage 2: Q items, cost ~ 200)
     int bestF = 2;
@@ -183,21 +177,6 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
     a.sm_amps = off; off = align16(off + 4 * T * bestF);
     a.sm_y = 0;
     a.sm_total = off;
-    // lane-per-frame initial guess: tables + 4 warps x 32 staged rows
-    cg::InitArgs& ia = p->ia;
-    ia.T = T;
-    ia.row_stride = T | 1;
-    ia.n_outer = p->n_outer;
-    ia.inv_ref = p->d.inv_ref;
-    ia.u = p->d.u;
-    ia.outer_idx = p->d.outer_idx;
-    ia.u_mid = p->u_mid;
-    ia.du = p->du;
-    ia.span = p->span;
-    ia.x_mid = static_cast<float>(p->x_mid);
-    ia.x_scale = static_cast<float>(p->x_scale);
-    p->init_npad = npad;
-    p->init_smem = 4 * (2 * T + p->n_outer) + 4 * 4 * 32 * ia.row_stride;
     std::vector<float2> tw5(5);
     for (int j = 0; j < 5; ++j) {
         const double ang = -kTwoPi * static_cast<double>((p->r0 * j) % 10) / 10.0;
@@ -218,6 +197,45 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fr, 128, a.sm_total)) != cudaSuccess) return e;
     if (occ < 1) return cudaSuccess;
     p->grid_fast = p->num_sms * occ;
+    p->Q = Q;
+    p->fast_ok = true;
+    return cudaSuccess;
+}
+
+// Initial-guess and register/shared-memory LM kernels of the throughput
+// path, its streams and events.  They need only the teeth (T, abscissa,
+// outer set), so any readout can feed them.  Leaves fit_ok false when T is
+// beyond what the kernels were instantiated for.
+cudaError_t setup_fit_kernels(cg_plan_s* p)
+{
+    p->fit_ok = false;
+    const int T = p->T;
+    // LM lanes per frame: one lane per frame for T <= 100 (no reductions),
+    // else 4 or 8 lanes with shuffle reductions
+    int G = p->opts.lanes_per_frame ? p->opts.lanes_per_frame : (T <= 100 ? 1 : (T <= 112 ? 4 : 8));
+    bool exact = false;
+    int ppl = cg::fit2_ppl(G, T, &exact);
+    while (ppl == 0 && G < 32 && !p->opts.lanes_per_frame) ppl = cg::fit2_ppl(G *= 2, T, &exact);
+    if (ppl == 0) return cudaSuccess;
+    const int npad = cg::init_npad(p->n_outer);
+    if (npad == 0) return cudaSuccess;
+    // lane-per-frame initial guess: tables + 4 warps x 32 staged rows
+    cg::InitArgs& ia = p->ia;
+    ia.T = T;
+    ia.row_stride = T | 1;
+    ia.n_outer = p->n_outer;
+    ia.inv_ref = p->d.inv_ref;
+    ia.u = p->d.u;
+    ia.outer_idx = p->d.outer_idx;
+    ia.u_mid = p->u_mid;
+    ia.du = p->du;
+    ia.span = p->span;
+    ia.x_mid = static_cast<float>(p->x_mid);
+    ia.x_scale = static_cast<float>(p->x_scale);
+    p->init_npad = npad;
+    p->init_smem = 4 * (2 * T + p->n_outer) + 4 * 4 * 32 * ia.row_stride;
+    cudaError_t e;
+    int occ = 0;
     void* ff = cg::fit2_ptr(G, ppl, exact);
     const size_t fsm = cg::fit2_smem(G, T);
     if ((e = cudaFuncSetAttribute(ff, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(fsm))) != cudaSuccess) return e;
@@ -235,13 +253,12 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
     if ((e = cudaStreamCreateWithFlags(&p->s_fit, cudaStreamNonBlocking)) != cudaSuccess) return e;
     for (cudaEvent_t* ev : {&p->ev_fork, &p->ev_read, &p->ev_join_r, &p->ev_join_f})
         if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
-    p->Q = Q;
     p->G2 = G;
     p->PPL = ppl;
     // 0: the whole call is one chunk (one launch per kernel; measured fastest
     // for large calls, since each kernel then has frames enough for every SM)
     p->chunk = p->opts.chunk_frames ? p->opts.chunk_frames : (int64_t(1) << 40);
-    p->fast_ok = true;
+    p->fit_ok = true;
     return cudaSuccess;
 }
 
@@ -271,6 +288,8 @@ void cg_opts_default(cg_opts* o)
     o->lanes_per_frame = 0;
     o->path = CG_PATH_AUTO;
     o->chunk_frames = 0;
+    o->sample_bits = 16;
+    o->solve_f64 = -1;
 }
 
 const char* cg_status_string(cg_status s)
@@ -315,7 +334,10 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         return fail(CG_ERR_ARG, "lanes_per_frame must be 0, 1, 2, 4, 8, 16 or 32");
     if (o.path < CG_PATH_AUTO || o.path > CG_PATH_PIPELINE) return fail(CG_ERR_ARG, "path must be a CG_PATH_* value");
     if (o.chunk_frames < 0) return fail(CG_ERR_ARG, "chunk_frames must be >= 0");
-    if (o.readout != CG_READOUT_FFT) return fail(CG_ERR_UNSUPPORTED, "readout kind %d not available", o.readout);
+    if (o.readout != CG_READOUT_FFT && o.readout != CG_READOUT_GEMM_SPLIT)
+        return fail(CG_ERR_ARG, "readout must be CG_READOUT_FFT or CG_READOUT_GEMM_SPLIT");
+    if (o.sample_bits != 12 && o.sample_bits != 16) return fail(CG_ERR_ARG, "sample_bits must be 12 or 16");
+    if (o.solve_f64 < -1 || o.solve_f64 > 1) return fail(CG_ERR_ARG, "solve_f64 must be -1, 0 or 1");
     if (o.init != CG_INIT_MOMENT) return fail(CG_ERR_UNSUPPORTED, "init kind %d not available", o.init);
     for (size_t i = 0; i < sizeof(o.reserved) / sizeof(o.reserved[0]); ++i)
         if (o.reserved[i] != 0) return fail(CG_ERR_ARG, "reserved option fields must be zero");
@@ -489,6 +511,22 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         delete p;
         return cuda_fail(e, "reference scratch");
     }
+    p->solve_f64 = (o.solve_f64 == -1) ? (o.readout == CG_READOUT_GEMM_SPLIT ? 1 : 0) : o.solve_f64;
+    if (o.readout == CG_READOUT_GEMM_SPLIT) {
+        p->gemm_split_x = (o.sample_bits == 12) ? 0 : 1;
+        if ((e = cg::setup_gemm(p)) != cudaSuccess) {
+            free_plan(p);
+            return cuda_fail(e, "tensor-core readout set-up");
+        }
+    }
+    if ((e = setup_fit_kernels(p)) != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "fit kernel set-up");
+    }
+    if (o.readout == CG_READOUT_GEMM_SPLIT && !p->fit_ok) {
+        free_plan(p);
+        return fail(CG_ERR_UNSUPPORTED, "n_teeth %d: no fit kernel for the tensor-core readout", T);
+    }
     if ((e = setup_fast(p, zidx)) != cudaSuccess) {
         free_plan(p);
         return cuda_fail(e, "throughput path set-up");
@@ -561,11 +599,13 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
     if (!amps || !params) return fail(CG_ERR_ARG, "amps_dev and params_dev are required");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
+    const bool gemm = p->opts.readout == CG_READOUT_GEMM_SPLIT;
     int path = p->opts.path;
     if (path == CG_PATH_AUTO) path = p->fast_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED;
     // the fast readout reads sample pairs as 32-bit words: frames 4-byte aligned
     if (path == CG_PATH_PIPELINE && (!p->fast_ok || (reinterpret_cast<uintptr_t>(frames) & 3)))
         path = CG_PATH_FUSED;
+    if (gemm) path = CG_PATH_PIPELINE;   // tensor-core readout, then initial guess and fit
     if (path == CG_PATH_PIPELINE) {
         // fork onto the plan's two streams; chunk c is read out on s_read while
         // chunk c-1 is fitted on s_fit (the readout leaves each frame's moment
@@ -576,8 +616,12 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
         for (int64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += p->chunk) {
             const int64_t m = (n - c0) < p->chunk ? (n - c0) : p->chunk;
             const int64_t T = p->T;
-            e = cg::launch_fast_readout(p, frames + c0 * p->N, m, amps + c0 * T, y ? y + c0 * T : nullptr,
-                                        p->s_read);
+            if (gemm)
+                e = cg::launch_gemm_readout(p, frames + c0 * p->N, m, amps + c0 * T, y ? y + c0 * T : nullptr,
+                                            p->s_read);
+            else
+                e = cg::launch_fast_readout(p, frames + c0 * p->N, m, amps + c0 * T, y ? y + c0 * T : nullptr,
+                                            p->s_read);
             if (e == cudaSuccess)
                 e = cg::launch_init(p, y ? y + c0 * T : nullptr, amps + c0 * T, m, params + c0 * 4,
                                     status ? status + c0 : nullptr, p->s_read);
@@ -610,7 +654,15 @@ cg_status cg_readout(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
     if (st != CG_OK) return st;
     if (n == 0) return CG_OK;
     if (!amps && !y) return fail(CG_ERR_ARG, "amps_dev and y_dev are both NULL");
-    cudaError_t e = cg::launch_readout(p, frames, n, amps, y, static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (p->opts.readout == CG_READOUT_GEMM_SPLIT)
+        e = cg::launch_gemm_readout(p, frames, n, amps, y, s);
+    else if (p->fast_ok && (p->opts.path == CG_PATH_AUTO || p->opts.path == CG_PATH_PIPELINE) &&
+             !(reinterpret_cast<uintptr_t>(frames) & 3))
+        e = cg::launch_fast_readout(p, frames, n, amps, y, s);
+    else
+        e = cg::launch_readout(p, frames, n, amps, y, s);
     if (e != cudaSuccess) return cuda_fail(e, "cg_readout launch");
     return CG_OK;
 }
@@ -644,3 +696,19 @@ cg_status cg_reference_accumulate(cg_plan_t p, const int16_t* frames, int64_t n,
 }
 
 }  // extern "C"
+
+extern "C" cg_status cg_check_device(cg_plan_t p)
+{
+    if (!p) return fail(CG_ERR_ARG, "plan is NULL");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != p->device) cudaSetDevice(p->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    int word = 0;
+    if (e == cudaSuccess && p->d.err) e = cudaMemcpy(&word, p->d.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && word != 0) e = cudaMemset(p->d.err, 0, sizeof(int));
+    if (prev >= 0 && prev != p->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(e, "cg_check_device");
+    if (word != 0) return fail(CG_ERR_DEVICE_CHECK, "a kernel's bounded wait ran out (code %d)", word);
+    return CG_OK;
+}

@@ -417,9 +417,22 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
         // ---- trial point ----
         float pe[4] = {p[0], p[1], p[2], p[3]};
         bool done = false;
-        if (f >= 0 && !fresh) {
-            float delta[4];
-            if (lm_solve4_fast(Nm, lambda, delta)) {
+        const bool trial = (f >= 0 && !fresh);
+        float delta[4] = {0.f, 0.f, 0.f, 0.f};
+        bool ok = true;
+        if (G > 1 && a.solve_f64) {
+            // FP64 is scarce: the group's leader solves, the group takes its step
+            int okl = 0;
+            if (trial && gl == 0) okl = lm_solve4_f64(Nm, lambda, delta) ? 1 : 0;
+            okl = __shfl_sync(kFull, okl, leader_lane);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) delta[i] = __shfl_sync(kFull, delta[i], leader_lane);
+            ok = okl != 0;
+        } else if (trial) {
+            ok = a.solve_f64 ? lm_solve4_f64(Nm, lambda, delta) : lm_solve4_fast(Nm, lambda, delta);
+        }
+        if (trial) {
+            if (ok) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) pe[i] = p[i] + delta[i];
             } else {
@@ -454,7 +467,7 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
                 ++it;
                 if (!(chi2t < INFINITY)) {
                     lambda *= 10.0f;
-                } else if (fabsf(chi2t - chi2) <= a.tol * chi2) {
+                } else if (chi2_settled(chi2t, chi2, a.tol, p[2], p[3])) {
                     if (chi2t <= chi2) {
 #pragma unroll
                         for (int i = 0; i < 4; ++i) p[i] = pe[i];
@@ -638,6 +651,7 @@ cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, i
     a.status = status;
     a.row_stride = p->T | 1;
     a.counter = p->d.fit_counter;
+    a.solve_f64 = p->solve_f64;
     // tasks are claimed dynamically: a few frames per lane group per task
     const int gpw = 32 / p->G2;                   // groups per warp
     a.task = 2 * gpw;

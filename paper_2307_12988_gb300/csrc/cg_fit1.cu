@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(128) fit1_kernel(Fit2Args a)
         bool done = false;
         if (fitting && !fresh) {
             float delta[4];
-            if (lm_solve4_fast(Nm, lambda, delta)) {
+            if (a.solve_f64 ? lm_solve4_f64(Nm, lambda, delta) : lm_solve4_fast(Nm, lambda, delta)) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) pe[i] = p[i] + delta[i];
             } else {
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(128) fit1_kernel(Fit2Args a)
                 ++it;
                 if (!(chi2t < INFINITY)) {
                     lambda *= 10.0f;
-                } else if (fabsf(chi2t - chi2) <= a.tol * chi2) {
+                } else if (chi2_settled(chi2t, chi2, a.tol, p[2], p[3])) {
                     if (chi2t <= chi2) {
 #pragma unroll
                         for (int i = 0; i < 4; ++i) p[i] = pe[i];

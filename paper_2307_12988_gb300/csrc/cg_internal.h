@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <string>
 #include <vector>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/combgpu.h"
@@ -83,6 +84,7 @@ struct Fit2Args {
     int T;
     int task;                // frames per warp task
     int row_stride;          // odd stride of the lane-per-frame spectrum slots
+    int solve_f64;           // 1: the 4x4 normal equations are solved in FP64
     unsigned long long* counter;  // next task (zeroed before the launch)
     const float* y;          // [n][T] normalised, or null
     const float* amps;       // [n][T] magnitudes when y is null
@@ -99,7 +101,28 @@ struct Fit2Args {
     int16_t* status;
 };
 
+// Arguments of the split-precision DFT-at-teeth GEMM readout.
+struct GemmArgs {
+    const int16_t* frames;
+    int64_t n;
+    int N, T;
+    int nkb;                 // K blocks of 64 samples
+    int ntile;               // output columns per tile (2 per tooth), multiple of 16
+    int nrows_total;         // rows of one (hi or lo) half of the twiddle matrix
+    int tmem_cols;           // TMEM columns allocated per block (n_acc * acc_cols)
+    int acc_cols;            // columns of one accumulator
+    int n_acc;               // accumulators the K blocks alternate over
+    int stages;              // pipeline depth
+    int vec8;                // frames 8-byte aligned and N % 4 == 0
+    const float* inv_ref;
+    float* amps;
+    float* y;
+    int* err;                // set to nonzero by a block whose bounded wait ran out
+};
+
 struct DevTables {
+    void* gemm_W = nullptr;       // [2][rows][Kpad] FP16 twiddles (hi, lo)
+    int* err = nullptr;           // device-side error word
     float2* tw_M5 = nullptr;
     int* tooth_of_m = nullptr;
     float2* tw_L = nullptr;
@@ -138,7 +161,13 @@ struct cg_plan_s {
     int grid_readout = 0, grid_fused = 0, grid_fit = 0;
     cg::ReadoutArgs ra{};
     // throughput path (fast readout + register-resident LM over chunks)
+    bool fit_ok = false;     // init + fit kernels of the throughput path configured
     bool fast_ok = false;    // geometry admits the fast readout
+    // split-precision GEMM readout
+    CUtensorMap gemm_map{};
+    int gemm_split_x = 1, gemm_smem = 0, gemm_ntiles = 0;
+    int solve_f64 = 0;
+    cg::GemmArgs ga{};
     int Q = 0;               // L = 10 Q
     int G2 = 4;              // LM lanes per frame of the register-resident fit
     int PPL = 0;             // LM points per lane
@@ -188,6 +217,11 @@ cudaError_t launch_init(const cg_plan_s* p, const float* y, const float* amps, i
 cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, int64_t n,
                         const float* p0, const int16_t* flags_in, float* params, float* rss,
                         int16_t* iters, int16_t* status, cudaStream_t s);
+
+// split-precision GEMM readout (cg_gemm.cu)
+cudaError_t setup_gemm(cg_plan_s* p);
+cudaError_t launch_gemm_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps, float* y,
+                                cudaStream_t s);
 
 // sets the thread-local text returned by cg_last_error()
 void set_last_error(const char* msg);
