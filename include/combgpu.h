@@ -56,6 +56,9 @@ typedef enum cg_status {
 #define CG_FIT_SINGULAR 2     /* J^T J not positive definite */
 #define CG_FIT_NONFINITE 3    /* the spectrum or chi^2 at the start is not finite */
 #define CG_FIT_INIT_FLAT 0x10 /* flag: moment initial guess saw a flat spectrum */
+#define CG_FIT_FALLBACK 0x20  /* flag: the learned initial guess and its polish steps
+                                 did not converge; the frame was refit by the full LM
+                                 from the moment initial guess */
 
 enum { CG_READOUT_FFT = 0, CG_READOUT_GEMM_SPLIT = 1 };
 enum { CG_FFT_AUTO = 0, CG_FFT_FULL = 1, CG_FFT_COSET = 2 };
@@ -89,7 +92,10 @@ typedef struct cg_opts {
                              full int16, split into 256 hi + lo (four products) */
     int solve_f64;        /* -1 (default): FP64 4x4 LM solve with the GEMM readout,
                              FP32 otherwise; 0: FP32; 1: FP64 */
-    int reserved[5];      /* must be zero */
+    int polish_iter;      /* CG_INIT_MLP: LM trial steps from the learned initial
+                             guess before a frame falls back to the full LM from
+                             the moment guess; 0 = 2 */
+    int reserved[4];      /* must be zero */
 } cg_opts;
 
 typedef struct cg_plan_s* cg_plan_t;
@@ -224,6 +230,128 @@ cg_status cg_reference_accumulate_noalloc(cg_plan_t plan, const int16_t* frames_
  * CG_ERR_DEVICE_CHECK (or CG_ERR_CUDA if the synchronisation fails).
  */
 cg_status cg_check_device(cg_plan_t plan);
+
+/*
+ * Per-kernel timing (diagnostics).  While enabled, cg_process records a pair
+ * of CUDA events around every kernel it launches, on the stream it launches
+ * that kernel on.  cg_timing_collect waits for the recorded events, returns
+ * the summed milliseconds and launch counts per stage since the last collect
+ * (ms_host, launches_host: arrays of CG_N_STAGES, either may be NULL) and
+ * forgets them.  Enabling costs two event records per launch.
+ */
+enum {
+    CG_STAGE_READOUT = 0,   /* cast + transform + tooth readout (FFT or GEMM) */
+    CG_STAGE_INIT = 1,      /* moment initial guess */
+    CG_STAGE_MLP = 2,       /* learned initial guess */
+    CG_STAGE_FIT = 3,       /* LM (full, or the polish steps after the MLP) */
+    CG_STAGE_FALLBACK = 4,  /* moment guess + full LM of frames the polish left */
+    CG_STAGE_FUSED = 5,     /* single-kernel path */
+    CG_N_STAGES = 8
+};
+cg_status cg_timing_enable(cg_plan_t plan, int enable);
+cg_status cg_timing_collect(cg_plan_t plan, double* ms_host, int64_t* launches_host);
+
+/*
+ * ---- Learned initial guess -------------------------------------------------
+ * A multilayer perceptron n_in -> H -> H -> n_out with tanh-form GELU hidden
+ * activations (z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))) and a linear
+ * output maps a normalised spectrum to the LM starting point, so that the LM
+ * only polishes (the paper notes that the iteration count depends on the
+ * initial parameters; it seeds them from filtered data instead).
+ *
+ * Training object (cg_mlp_t): FP32 master parameters, gradients and Adam
+ * moments on the current device, trained by the library's own kernels.  Flat
+ * parameter order: W1 [H][n_in], b1 [H], W2 [H][H], b2 [H], W3 [n_out][H],
+ * b3 [n_out], row-major.  Inputs and targets given to the training calls are
+ * already standardised by the caller; the standardisation vectors travel in
+ * the saved blob and are applied by cg_mlp_load's inference kernel.
+ */
+typedef struct cg_mlp_s* cg_mlp_t;
+
+/* Number of parameters of an (n_in, n_hidden, n_out) network. */
+int64_t cg_mlp_param_count(int n_in, int n_hidden, int n_out);
+
+/*
+ * cg_mlp_create -- allocate a network for batches of up to max_batch rows.
+ * 1 <= n_in, n_hidden <= 1024; 1 <= n_out <= 16; 1 <= max_batch <= 1<<20.
+ * Weights are drawn uniformly from +-1/sqrt(fan_in) by a counter-based hash
+ * (SplitMix64) of (seed, parameter index); biases are zero; Adam state zero.
+ */
+cg_status cg_mlp_create(cg_mlp_t* mlp, int n_in, int n_hidden, int n_out, int max_batch,
+                        uint64_t seed);
+void cg_mlp_destroy(cg_mlp_t mlp);
+
+/* Copy the parameters to / from host float [count]; count must equal
+ * cg_mlp_param_count.  set_params also clears the Adam state. Synchronous. */
+cg_status cg_mlp_get_params(cg_mlp_t mlp, float* params_host, int64_t count);
+cg_status cg_mlp_set_params(cg_mlp_t mlp, const float* params_host, int64_t count);
+
+/* FP32 forward pass: x_dev float [n][n_in] -> out_dev float [n][n_out]
+ * (any n >= 0; processed in slices of max_batch).  Asynchronous. */
+cg_status cg_mlp_forward(cg_mlp_t mlp, const float* x_dev, int64_t n, float* out_dev,
+                         void* cuda_stream);
+
+/*
+ * cg_mlp_backward -- loss L = mean over rows and outputs of (out - t)^2 and
+ * its gradient for one batch (1 <= n <= max_batch): x_dev [n][n_in], t_dev
+ * [n][n_out].  The gradient stays in the object for cg_mlp_adam; grad_dev
+ * (float [param_count]) and loss_dev (float [1]) receive copies when not NULL.
+ * Deterministic: no atomics, fixed summation order.  Asynchronous.
+ */
+cg_status cg_mlp_backward(cg_mlp_t mlp, const float* x_dev, const float* t_dev, int64_t n,
+                          float* loss_dev, float* grad_dev, void* cuda_stream);
+
+/* One Adam step (Kingma & Ba 2015) on the stored gradient, bias-corrected,
+ * step counter kept in the object.  Asynchronous. */
+cg_status cg_mlp_adam(cg_mlp_t mlp, float lr, float beta1, float beta2, float eps,
+                      void* cuda_stream);
+
+/*
+ * cg_mlp_train_epoch -- minibatch loop on the device: for each batch b of
+ * `batch` rows (the last may be shorter) gathers rows perm_dev[b*batch ...]
+ * of x_dev / t_dev, runs cg_mlp_backward and cg_mlp_adam(lr, 0.9, 0.999,
+ * 1e-8).  perm_dev int32 [n] (a permutation of 0..n-1 chosen by the caller;
+ * an entry outside [0, n) contributes a zero row);
+ * losses_dev float [ceil(n / batch)] or NULL receives each batch's loss.
+ * 1 <= batch <= max_batch.  Asynchronous.
+ */
+cg_status cg_mlp_train_epoch(cg_mlp_t mlp, const float* x_dev, const float* t_dev, int64_t n,
+                             const int32_t* perm_dev, int batch, float lr, float* losses_dev,
+                             void* cuda_stream);
+
+/* Standardisation stored with the network (host arrays): the network's input
+ * is (y - in_mean) * in_scale, its output o maps to o * out_scale + out_mean. */
+cg_status cg_mlp_set_norm(cg_mlp_t mlp, const float* in_mean, const float* in_scale,
+                          const float* out_mean, const float* out_scale);
+
+/*
+ * cg_mlp_save -- serialise (synchronous) into blob_host of capacity bytes:
+ * header "CGMLP001", int32 n_in, n_hidden, n_out, 0, then float in_mean[n_in],
+ * in_scale[n_in], out_mean[n_out], out_scale[n_out], params[param_count],
+ * little-endian.  *bytes_out receives the size (call with blob_host NULL to
+ * ask for it).
+ */
+cg_status cg_mlp_save(cg_mlp_t mlp, void* blob_host, size_t capacity, size_t* bytes_out);
+
+/*
+ * cg_mlp_load -- give a plan the learned initial guess from a blob written by
+ * cg_mlp_save.  The network must have n_in == n_teeth (inputs in the plan's
+ * tooth order), n_hidden == 256, n_out == 4 with outputs (c, g, A, B) in
+ * abscissa units.  Weights are stored on the device in BF16 for the
+ * tensor-core inference kernel (FP32 accumulation); biases and the output
+ * layer stay FP32.  Required before cg_process with init = CG_INIT_MLP.
+ * Errors: CG_ERR_ARG (malformed blob, shape mismatch), CG_ERR_CUDA.
+ */
+cg_status cg_mlp_load(cg_plan_t plan, const void* blob_host, size_t bytes);
+
+/*
+ * cg_mlp_infer -- only the learned initial guess of cg_process: y_dev float
+ * [n][T] normalised spectra -> p0_dev float [n][4] (c, g, A, B) in abscissa
+ * units, g clamped to [dx/2, span/2] as the moment guess is.  Asynchronous.
+ * CG_ERR_STATE if no network is loaded.
+ */
+cg_status cg_mlp_infer(cg_plan_t plan, const float* y_dev, int64_t n, float* p0_dev,
+                       void* cuda_stream);
 
 /* Text of a status code (static storage). */
 const char* cg_status_string(cg_status status);

@@ -14,12 +14,16 @@ from . import _binding
 from ._binding import (CgError, cg_check_device, cg_fit, cg_opts_default, cg_plan, cg_plan_describe,
                        cg_plan_destroy, cg_process, cg_readout, cg_reference_accumulate,
                        cg_set_reference, cg_status_string, cg_version, load)
-from ._binding import (FFT_AUTO, FFT_COSET, FFT_FULL, FIT_CONVERGED, FIT_INIT_FLAT,
+from ._binding import (cg_mlp_adam, cg_mlp_backward, cg_mlp_create, cg_mlp_destroy, cg_mlp_forward,
+                       cg_mlp_get_params, cg_mlp_infer, cg_mlp_load, cg_mlp_param_count, cg_mlp_save,
+                       cg_mlp_set_norm, cg_mlp_set_params, cg_mlp_train_epoch, cg_timing_collect,
+                       cg_timing_enable)
+from ._binding import (FFT_AUTO, FFT_COSET, FFT_FULL, FIT_CONVERGED, FIT_FALLBACK, FIT_INIT_FLAT,
                        FIT_MAX_ITER, FIT_NONFINITE, FIT_SINGULAR, INIT_MLP, INIT_MOMENT,
                        READOUT_FFT, READOUT_GEMM_SPLIT, PATH_AUTO, PATH_FUSED, PATH_SPLIT,
                        PATH_PIPELINE)
 
-__all__ = ["Plan", "CgError", "load", "cg_plan", "cg_plan_destroy", "cg_plan_describe",
+__all__ = ["Plan", "Mlp", "CgError", "load", "cg_plan", "cg_plan_destroy", "cg_plan_describe",
            "cg_process", "cg_readout", "cg_fit", "cg_reference_accumulate",
            "cg_set_reference", "cg_opts_default", "cg_status_string", "cg_version"]
 
@@ -98,3 +102,78 @@ class Plan:
 
     def reference_accumulate(self, frames, stream=None) -> np.ndarray:
         return cg_reference_accumulate(self.handle, frames, frames.shape[0], stream)
+
+    def mlp_load(self, blob: bytes):
+        """Attach a learned initial guess (a ``cg_mlp_save`` blob)."""
+        cg_mlp_load(self.handle, blob)
+
+    def mlp_infer(self, y, stream=None):
+        """Learned initial guess p0 [n, 4] for normalised spectra y [n, T]."""
+        import torch
+        p0 = torch.empty((y.shape[0], 4), dtype=torch.float32, device=y.device)
+        cg_mlp_infer(self.handle, y, y.shape[0], p0, stream)
+        return p0
+
+    def timing(self, enable: bool = True):
+        cg_timing_enable(self.handle, enable)
+
+    def timing_collect(self) -> dict:
+        return cg_timing_collect(self.handle)
+
+
+class Mlp:
+    """Network of the learned initial guess, trained on the device by the
+    library's kernels (``cg_mlp_*``).  Inputs and targets are standardised
+    by the caller; ``set_norm`` stores the standardisation with the blob."""
+
+    def __init__(self, n_in, n_hidden=256, n_out=4, max_batch=4096, seed=0):
+        self.n_in, self.n_hidden, self.n_out, self.max_batch = n_in, n_hidden, n_out, max_batch
+        self.n_params = cg_mlp_param_count(n_in, n_hidden, n_out)
+        self.handle = cg_mlp_create(n_in, n_hidden, n_out, max_batch, seed)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cg_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        return cg_mlp_get_params(self.handle, self.n_params)
+
+    def set_params(self, theta):
+        cg_mlp_set_params(self.handle, theta)
+
+    def forward(self, x, stream=None):
+        import torch
+        out = torch.empty((x.shape[0], self.n_out), dtype=torch.float32, device=x.device)
+        cg_mlp_forward(self.handle, x, x.shape[0], out, stream)
+        return out
+
+    def backward(self, x, t, stream=None):
+        """(loss tensor [1], gradient tensor [n_params]) of one batch."""
+        import torch
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        grad = torch.empty(self.n_params, dtype=torch.float32, device=x.device)
+        cg_mlp_backward(self.handle, x, t, x.shape[0], loss, grad, stream)
+        return loss, grad
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        cg_mlp_adam(self.handle, lr, beta1, beta2, eps, stream)
+
+    def train_epoch(self, x, t, perm, batch, lr, stream=None):
+        import torch
+        nb = (x.shape[0] + batch - 1) // batch
+        losses = torch.empty(nb, dtype=torch.float32, device=x.device)
+        cg_mlp_train_epoch(self.handle, x, t, x.shape[0], perm, batch, lr, losses, stream)
+        return losses
+
+    def set_norm(self, in_mean, in_scale, out_mean, out_scale):
+        cg_mlp_set_norm(self.handle, in_mean, in_scale, out_mean, out_scale)
+
+    def save(self) -> bytes:
+        return cg_mlp_save(self.handle)

@@ -24,6 +24,10 @@ STATUS_NAMES = {0: "CG_OK", 1: "CG_ERR_ARG", 2: "CG_ERR_CUDA", 3: "CG_ERR_NOMEM"
                 4: "CG_ERR_TOOTH_RANGE", 5: "CG_ERR_OVERFLOW", 6: "CG_ERR_TIMEOUT",
                 7: "CG_ERR_DEVICE_CHECK", 8: "CG_ERR_UNSUPPORTED", 9: "CG_ERR_STATE"}
 FIT_CONVERGED, FIT_MAX_ITER, FIT_SINGULAR, FIT_NONFINITE, FIT_INIT_FLAT = 0, 1, 2, 3, 0x10
+FIT_FALLBACK = 0x20
+STAGE_READOUT, STAGE_INIT, STAGE_MLP, STAGE_FIT, STAGE_FALLBACK, STAGE_FUSED = 0, 1, 2, 3, 4, 5
+N_STAGES = 8
+STAGE_NAMES = {0: "readout", 1: "init", 2: "mlp", 3: "fit", 4: "fallback", 5: "fused"}
 READOUT_FFT, READOUT_GEMM_SPLIT = 0, 1
 FFT_AUTO, FFT_FULL, FFT_COSET = 0, 1, 2
 INIT_MOMENT, INIT_MLP = 0, 1
@@ -44,7 +48,7 @@ class cg_opts(ctypes.Structure):
                 ("lambda0", ctypes.c_double), ("lanes_per_frame", ctypes.c_int),
                 ("path", ctypes.c_int), ("chunk_frames", ctypes.c_int),
                 ("sample_bits", ctypes.c_int), ("solve_f64", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("polish_iter", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class cg_plan_info(ctypes.Structure):
@@ -70,6 +74,24 @@ _SIGS = {
     "cg_reference_accumulate": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     "cg_reference_accumulate_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     "cg_check_device": (ctypes.c_int, [_P]),
+    "cg_timing_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cg_timing_collect": (ctypes.c_int, [_P, _P, _P]),
+    "cg_mlp_param_count": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "cg_mlp_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_uint64]),
+    "cg_mlp_destroy": (None, [_P]),
+    "cg_mlp_get_params": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "cg_mlp_set_params": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "cg_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    "cg_mlp_backward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P, _P]),
+    "cg_mlp_adam": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   _P]),
+    "cg_mlp_train_epoch": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, ctypes.c_int, ctypes.c_float,
+                                          _P, _P]),
+    "cg_mlp_set_norm": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "cg_mlp_save": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "cg_mlp_load": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "cg_mlp_infer": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     "cg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cg_last_error": (ctypes.c_char_p, []),
     "cg_version": (ctypes.c_int, []),
@@ -220,6 +242,88 @@ def cg_reference_accumulate_noalloc(plan: int, frames, n: int, ref_dev, stream=N
 def cg_check_device(plan: int) -> None:
     """Synchronise and raise CgError if a kernel recorded a device-side error."""
     _check(load().cg_check_device(plan), "cg_check_device")
+
+
+def cg_timing_enable(plan: int, enable: bool) -> None:
+    _check(load().cg_timing_enable(plan, 1 if enable else 0), "cg_timing_enable")
+
+
+def cg_timing_collect(plan: int) -> dict:
+    """{stage name: (total ms, launches)} since the last collect."""
+    ms = np.zeros(N_STAGES, dtype=np.float64)
+    cnt = np.zeros(N_STAGES, dtype=np.int64)
+    _check(load().cg_timing_collect(plan, _ptr(ms), _ptr(cnt)), "cg_timing_collect")
+    return {STAGE_NAMES[i]: (float(ms[i]), int(cnt[i])) for i in STAGE_NAMES if cnt[i] > 0}
+
+
+def cg_mlp_param_count(n_in: int, n_hidden: int, n_out: int) -> int:
+    return int(load().cg_mlp_param_count(int(n_in), int(n_hidden), int(n_out)))
+
+
+def cg_mlp_create(n_in: int, n_hidden: int, n_out: int, max_batch: int, seed: int) -> int:
+    h = _P()
+    _check(load().cg_mlp_create(ctypes.byref(h), int(n_in), int(n_hidden), int(n_out), int(max_batch),
+                                int(seed) & 0xFFFFFFFFFFFFFFFF), "cg_mlp_create")
+    return h.value
+
+
+def cg_mlp_destroy(mlp: int) -> None:
+    if mlp:
+        load().cg_mlp_destroy(mlp)
+
+
+def cg_mlp_get_params(mlp: int, count: int) -> np.ndarray:
+    out = np.empty(int(count), dtype=np.float32)
+    _check(load().cg_mlp_get_params(mlp, _ptr(out), int(count)), "cg_mlp_get_params")
+    return out
+
+
+def cg_mlp_set_params(mlp: int, params) -> None:
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().cg_mlp_set_params(mlp, _ptr(a), int(a.size)), "cg_mlp_set_params")
+
+
+def cg_mlp_forward(mlp: int, x, n: int, out, stream=None) -> None:
+    _check(load().cg_mlp_forward(mlp, _ptr(x), int(n), _ptr(out), _stream(stream)), "cg_mlp_forward")
+
+
+def cg_mlp_backward(mlp: int, x, t, n: int, loss=None, grad=None, stream=None) -> None:
+    _check(load().cg_mlp_backward(mlp, _ptr(x), _ptr(t), int(n), _ptr(loss), _ptr(grad), _stream(stream)),
+           "cg_mlp_backward")
+
+
+def cg_mlp_adam(mlp: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                stream=None) -> None:
+    _check(load().cg_mlp_adam(mlp, float(lr), float(beta1), float(beta2), float(eps), _stream(stream)),
+           "cg_mlp_adam")
+
+
+def cg_mlp_train_epoch(mlp: int, x, t, n: int, perm, batch: int, lr: float, losses=None,
+                       stream=None) -> None:
+    _check(load().cg_mlp_train_epoch(mlp, _ptr(x), _ptr(t), int(n), _ptr(perm), int(batch), float(lr),
+                                     _ptr(losses), _stream(stream)), "cg_mlp_train_epoch")
+
+
+def cg_mlp_set_norm(mlp: int, in_mean, in_scale, out_mean, out_scale) -> None:
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (in_mean, in_scale, out_mean, out_scale)]
+    _check(load().cg_mlp_set_norm(mlp, *[_ptr(a) for a in arrs]), "cg_mlp_set_norm")
+
+
+def cg_mlp_save(mlp: int) -> bytes:
+    size = ctypes.c_size_t(0)
+    _check(load().cg_mlp_save(mlp, None, 0, ctypes.byref(size)), "cg_mlp_save")
+    buf = ctypes.create_string_buffer(size.value)
+    _check(load().cg_mlp_save(mlp, buf, size.value, ctypes.byref(size)), "cg_mlp_save")
+    return buf.raw[:size.value]
+
+
+def cg_mlp_load(plan: int, blob: bytes) -> None:
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    _check(load().cg_mlp_load(plan, buf, len(blob)), "cg_mlp_load")
+
+
+def cg_mlp_infer(plan: int, y, n: int, p0, stream=None) -> None:
+    _check(load().cg_mlp_infer(plan, _ptr(y), int(n), _ptr(p0), _stream(stream)), "cg_mlp_infer")
 
 
 def cg_status_string(status: int) -> str:

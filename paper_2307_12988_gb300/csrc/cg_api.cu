@@ -121,6 +121,10 @@ void free_tables(cg::DevTables& d)
     cudaFree(d.fit_counter);
     cudaFree(d.gemm_W);
     cudaFree(d.err);
+    cudaFree(d.mlp_W);
+    cudaFree(d.mlp_tab);
+    cudaFree(d.fb_list);
+    cudaFree(d.fb_count);
     d = cg::DevTables{};
 }
 
@@ -131,6 +135,11 @@ void free_plan(cg_plan_s* p)
     if (p->s_fit) cudaStreamDestroy(p->s_fit);
     for (cudaEvent_t e : {p->ev_fork, p->ev_read, p->ev_join_r, p->ev_join_f})
         if (e) cudaEventDestroy(e);
+    for (const auto& t : p->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     delete p;
 }
 
@@ -273,6 +282,32 @@ std::vector<float> inv_ref_of(const std::vector<double>& ref)
 
 void cg::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
+namespace {
+
+// runs launch(); with the plan's timing on, brackets it by two CUDA events
+// recorded on the stream the kernel is launched on
+template <class F>
+cudaError_t timed(cg_plan_s* p, int stage, cudaStream_t s, F&& launch)
+{
+    if (!p->timing) return launch();
+    cudaEvent_t ev[2];
+    for (cudaEvent_t& x : ev) {
+        if (!p->ev_pool.empty()) {
+            x = p->ev_pool.back();
+            p->ev_pool.pop_back();
+        } else if (cudaError_t r = cudaEventCreate(&x); r != cudaSuccess) {
+            return r;
+        }
+    }
+    cudaError_t e = cudaEventRecord(ev[0], s);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+    p->timed.push_back({stage, ev[0], ev[1]});
+    return e;
+}
+
+}  // namespace
+
 extern "C" {
 
 void cg_opts_default(cg_opts* o)
@@ -338,7 +373,9 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         return fail(CG_ERR_ARG, "readout must be CG_READOUT_FFT or CG_READOUT_GEMM_SPLIT");
     if (o.sample_bits != 12 && o.sample_bits != 16) return fail(CG_ERR_ARG, "sample_bits must be 12 or 16");
     if (o.solve_f64 < -1 || o.solve_f64 > 1) return fail(CG_ERR_ARG, "solve_f64 must be -1, 0 or 1");
-    if (o.init != CG_INIT_MOMENT) return fail(CG_ERR_UNSUPPORTED, "init kind %d not available", o.init);
+    if (o.init != CG_INIT_MOMENT && o.init != CG_INIT_MLP) return fail(CG_ERR_ARG, "init must be CG_INIT_MOMENT or CG_INIT_MLP");
+    if (o.polish_iter < 0 || o.polish_iter > 32767) return fail(CG_ERR_ARG, "polish_iter outside [0, 32767]");
+    if (o.polish_iter == 0) o.polish_iter = 2;
     for (size_t i = 0; i < sizeof(o.reserved) / sizeof(o.reserved[0]); ++i)
         if (o.reserved[i] != 0) return fail(CG_ERR_ARG, "reserved option fields must be zero");
 
@@ -531,6 +568,10 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         free_plan(p);
         return cuda_fail(e, "throughput path set-up");
     }
+    if (o.init == CG_INIT_MLP && (!p->fit_ok || (o.readout == CG_READOUT_FFT && !p->fast_ok) || T > 256)) {
+        free_plan(p);
+        return fail(CG_ERR_UNSUPPORTED, "the learned initial guess needs the pipelined path and n_teeth <= 256");
+    }
     *out = p;
     return CG_OK;
 }
@@ -600,49 +641,100 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     const bool gemm = p->opts.readout == CG_READOUT_GEMM_SPLIT;
+    const bool mlp = p->opts.init == CG_INIT_MLP;
+    if (mlp && !p->mlp_ok) return fail(CG_ERR_STATE, "init is CG_INIT_MLP but no network is loaded (cg_mlp_load)");
     int path = p->opts.path;
     if (path == CG_PATH_AUTO) path = p->fast_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED;
     // the fast readout reads sample pairs as 32-bit words: frames 4-byte aligned
     if (path == CG_PATH_PIPELINE && (!p->fast_ok || (reinterpret_cast<uintptr_t>(frames) & 3)))
         path = CG_PATH_FUSED;
-    if (gemm) path = CG_PATH_PIPELINE;   // tensor-core readout, then initial guess and fit
+    // tensor-core readout or learned guess: readout, then guess and fit kernels
+    if (gemm || mlp) path = CG_PATH_PIPELINE;
+    if (mlp && !gemm && (reinterpret_cast<uintptr_t>(frames) & 3))
+        return fail(CG_ERR_ARG, "frames_dev must be 4-byte aligned with the learned initial guess");
     if (path == CG_PATH_PIPELINE) {
-        // fork onto the plan's two streams; chunk c is read out on s_read while
-        // chunk c-1 is fitted on s_fit (the readout leaves each frame's moment
-        // initial guess in params and its flag in status for the fit)
+        const int64_t cmax = n < p->chunk ? n : p->chunk;
+        if (mlp && p->d.fb_cap < cmax) {
+            // frames left by the polish of one chunk (grows, never shrinks)
+            cudaFree(p->d.fb_list);
+            p->d.fb_list = nullptr;
+            p->d.fb_cap = 0;
+            if ((e = cudaMalloc(&p->d.fb_list, sizeof(int) * cmax)) != cudaSuccess) return cuda_fail(e, "fallback list");
+            if (!p->d.fb_count && (e = cudaMalloc(&p->d.fb_count, sizeof(int))) != cudaSuccess)
+                return cuda_fail(e, "fallback count");
+            p->d.fb_cap = cmax;
+        }
+        // fork onto the plan's two streams; chunk c is read out (and its
+        // initial guess made) on s_read while chunk c-1 is fitted on s_fit; the
+        // guess goes to params and its flag to status, where the fit reads them
         e = cudaEventRecord(p->ev_fork, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_read, p->ev_fork, 0);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_fit, p->ev_fork, 0);
         for (int64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += p->chunk) {
             const int64_t m = (n - c0) < p->chunk ? (n - c0) : p->chunk;
             const int64_t T = p->T;
-            if (gemm)
-                e = cg::launch_gemm_readout(p, frames + c0 * p->N, m, amps + c0 * T, y ? y + c0 * T : nullptr,
-                                            p->s_read);
-            else
-                e = cg::launch_fast_readout(p, frames + c0 * p->N, m, amps + c0 * T, y ? y + c0 * T : nullptr,
-                                            p->s_read);
-            if (e == cudaSuccess)
-                e = cg::launch_init(p, y ? y + c0 * T : nullptr, amps + c0 * T, m, params + c0 * 4,
-                                    status ? status + c0 : nullptr, p->s_read);
+            const int16_t* fc = frames + c0 * p->N;
+            float* ac = amps + c0 * T;
+            float* yc = y ? y + c0 * T : nullptr;
+            float* pc = params + c0 * 4;
+            float* rc = rss ? rss + c0 : nullptr;
+            int16_t* ic = iters ? iters + c0 : nullptr;
+            int16_t* sc = status ? status + c0 : nullptr;
+            e = timed(p, CG_STAGE_READOUT, p->s_read, [&] {
+                return gemm ? cg::launch_gemm_readout(p, fc, m, ac, yc, p->s_read)
+                            : cg::launch_fast_readout(p, fc, m, ac, yc, p->s_read);
+            });
+            if (e == cudaSuccess && mlp)
+                e = timed(p, CG_STAGE_MLP, p->s_read, [&] { return cg::launch_mlp(p, yc, ac, m, pc, sc, p->s_read); });
+            else if (e == cudaSuccess)
+                e = timed(p, CG_STAGE_INIT, p->s_read,
+                          [&] { return cg::launch_init(p, yc, ac, m, pc, sc, p->s_read, nullptr, nullptr); });
             if (e == cudaSuccess) e = cudaEventRecord(p->ev_read, p->s_read);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_fit, p->ev_read, 0);
-            if (e == cudaSuccess)
-                e = cg::launch_fit2(p, y ? y + c0 * T : nullptr, amps + c0 * T, m, params + c0 * 4,
-                                    status ? status + c0 : nullptr, params + c0 * 4,
-                                    rss ? rss + c0 : nullptr, iters ? iters + c0 : nullptr,
-                                    status ? status + c0 : nullptr, p->s_fit);
+            if (e == cudaSuccess && mlp) {
+                // polish steps from the learned guess; frames that do not
+                // converge are listed and refit by the full LM from the moment
+                // guess
+                cg::FitLaunch pol;
+                pol.max_iter = p->opts.polish_iter < p->opts.max_iter ? p->opts.polish_iter : p->opts.max_iter;
+                pol.fb_list = p->d.fb_list;
+                pol.fb_count = p->d.fb_count;
+                e = cudaMemsetAsync(p->d.fb_count, 0, sizeof(int), p->s_fit);
+                if (e == cudaSuccess)
+                    e = timed(p, CG_STAGE_FIT, p->s_fit, [&] {
+                        return cg::launch_fit2(p, yc, ac, m, pc, sc, pc, rc, ic, sc, p->s_fit, pol);
+                    });
+                if (e == cudaSuccess)
+                    e = timed(p, CG_STAGE_FALLBACK, p->s_fit, [&] {
+                        return cg::launch_init(p, yc, ac, m, pc, sc, p->s_fit, p->d.fb_list, p->d.fb_count);
+                    });
+                cg::FitLaunch fb;
+                fb.list = p->d.fb_list;
+                fb.list_n = p->d.fb_count;
+                fb.iters_base = pol.max_iter;
+                fb.status_or = CG_FIT_FALLBACK;
+                if (e == cudaSuccess)
+                    e = timed(p, CG_STAGE_FALLBACK, p->s_fit, [&] {
+                        return cg::launch_fit2(p, yc, ac, m, pc, sc, pc, rc, ic, sc, p->s_fit, fb);
+                    });
+            } else if (e == cudaSuccess) {
+                e = timed(p, CG_STAGE_FIT, p->s_fit,
+                          [&] { return cg::launch_fit2(p, yc, ac, m, pc, sc, pc, rc, ic, sc, p->s_fit); });
+            }
         }
         if (e == cudaSuccess) e = cudaEventRecord(p->ev_join_r, p->s_read);
         if (e == cudaSuccess) e = cudaEventRecord(p->ev_join_f, p->s_fit);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join_r, 0);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join_f, 0);
     } else if (path == CG_PATH_FUSED) {
-        e = cg::launch_fused(p, frames, n, amps, y, params, rss, iters, status, s);
+        e = timed(p, CG_STAGE_FUSED, s,
+                  [&] { return cg::launch_fused(p, frames, n, amps, y, params, rss, iters, status, s); });
     } else {
-        e = cg::launch_readout(p, frames, n, amps, y, s);
+        e = timed(p, CG_STAGE_READOUT, s, [&] { return cg::launch_readout(p, frames, n, amps, y, s); });
         // without y_dev the fit reads the magnitudes and applies the reference itself
-        if (e == cudaSuccess) e = cg::launch_fit(p, y, amps, n, nullptr, params, rss, iters, status, s);
+        if (e == cudaSuccess)
+            e = timed(p, CG_STAGE_FIT, s,
+                      [&] { return cg::launch_fit(p, y, amps, n, nullptr, params, rss, iters, status, s); });
     }
     if (e != cudaSuccess) return cuda_fail(e, "cg_process launch");
     return CG_OK;
@@ -710,5 +802,71 @@ extern "C" cg_status cg_check_device(cg_plan_t p)
     if (prev >= 0 && prev != p->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return cuda_fail(e, "cg_check_device");
     if (word != 0) return fail(CG_ERR_DEVICE_CHECK, "a kernel's bounded wait ran out (code %d)", word);
+    return CG_OK;
+}
+
+extern "C" cg_status cg_mlp_load(cg_plan_t p, const void* blob, size_t bytes)
+{
+    if (!p || !blob) return fail(CG_ERR_ARG, "plan or blob is NULL");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != p->device) cudaSetDevice(p->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    const char* why = nullptr;
+    if (e == cudaSuccess) e = cg::setup_mlp(p, static_cast<const unsigned char*>(blob), bytes, &why);
+    if (prev >= 0 && prev != p->device) cudaSetDevice(prev);
+    if (why) {
+        p->mlp_ok = false;
+        return fail(e == cudaErrorInvalidValue ? CG_ERR_ARG : CG_ERR_CUDA, "cg_mlp_load: %s", why);
+    }
+    if (e != cudaSuccess) {
+        p->mlp_ok = false;
+        return cuda_fail(e, "cg_mlp_load");
+    }
+    return CG_OK;
+}
+
+extern "C" cg_status cg_mlp_infer(cg_plan_t p, const float* y, int64_t n, float* p0, void* stream)
+{
+    if (!p) return fail(CG_ERR_ARG, "plan is NULL");
+    if (n < 0) return fail(CG_ERR_ARG, "n < 0");
+    if (!p->mlp_ok) return fail(CG_ERR_STATE, "no network is loaded (cg_mlp_load)");
+    if (n == 0) return CG_OK;
+    if (!y || !p0) return fail(CG_ERR_ARG, "y_dev and p0_dev are required");
+    cudaError_t e = cg::launch_mlp(p, y, nullptr, n, p0, nullptr, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cg_mlp_infer launch");
+    return CG_OK;
+}
+
+extern "C" cg_status cg_timing_enable(cg_plan_t p, int enable)
+{
+    if (!p) return fail(CG_ERR_ARG, "plan is NULL");
+    p->timing = enable != 0;
+    return CG_OK;
+}
+
+extern "C" cg_status cg_timing_collect(cg_plan_t p, double* ms, int64_t* launches)
+{
+    if (!p) return fail(CG_ERR_ARG, "plan is NULL");
+    double acc[CG_N_STAGES] = {0};
+    int64_t cnt[CG_N_STAGES] = {0};
+    cudaError_t e = cudaSuccess;
+    for (const auto& t : p->timed) {
+        if (e == cudaSuccess) e = cudaEventSynchronize(t.b);
+        float v = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&v, t.a, t.b);
+        if (e == cudaSuccess && t.stage >= 0 && t.stage < CG_N_STAGES) {
+            acc[t.stage] += v;
+            cnt[t.stage] += 1;
+        }
+        p->ev_pool.push_back(t.a);
+        p->ev_pool.push_back(t.b);
+    }
+    p->timed.clear();
+    if (e != cudaSuccess) return cuda_fail(e, "cg_timing_collect");
+    for (int i = 0; i < CG_N_STAGES; ++i) {
+        if (ms) ms[i] = acc[i];
+        if (launches) launches[i] = cnt[i];
+    }
     return CG_OK;
 }

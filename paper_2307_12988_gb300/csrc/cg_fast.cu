@@ -234,14 +234,26 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
     const int lane = threadIdx.x & 31;
     constexpr OddEvenNet<NPAD> net{};
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    int64_t n = a.n;
+    if (a.list_n) {
+        const int64_t c = *a.list_n;
+        n = c < n ? c : n;
+    }
     for (int64_t task = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-         task * 32 < a.n; task += nwarps) {
+         task * 32 < n; task += nwarps) {
         const int64_t f0 = task * 32;
-        const int nf = (a.n - f0) < 32 ? static_cast<int>(a.n - f0) : 32;
-        // the 32 rows are contiguous in global memory: one flat coalesced
-        // sweep, eight loads in flight per lane, (frame, tooth) tracked
-        // incrementally
-        {
+        const int nf = (n - f0) < 32 ? static_cast<int>(n - f0) : 32;
+        if (a.list) {
+            // listed frames (the fallback pass): one coalesced row at a time
+            for (int f = 0; f < nf; ++f) {
+                const int64_t fr = a.list[f0 + f];
+                const float* src = (a.y ? a.y : a.amps) + fr * T;
+                for (int k = lane; k < T; k += 32) rows[f * TS + k] = a.y ? src[k] : src[k] * iref[k];
+            }
+        } else {
+            // the 32 rows are contiguous in global memory: one flat coalesced
+            // sweep, eight loads in flight per lane, (frame, tooth) tracked
+            // incrementally
             const float* src = (a.y ? a.y : a.amps) + f0 * T;
             const int total = nf * T;
             int f = lane / T, k = lane - (lane / T) * T;
@@ -266,6 +278,7 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
         }
         __syncwarp();
         if (lane < nf) {
+            const int64_t fo = a.list ? static_cast<int64_t>(a.list[f0 + lane]) : f0 + lane;
             const float* r = rows + lane * TS;
             float v[NPAD];
 #pragma unroll
@@ -312,12 +325,12 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
                 g0 = fminf(fmaxf(g0, 0.5f * a.du), 0.5f * a.span);
                 c0 = Wu / W;
             }
-            float* po = a.p0_out + (f0 + lane) * 4;
+            float* po = a.p0_out + fo * 4;
             po[0] = fmaf(a.x_scale, c0, a.x_mid);
             po[1] = a.x_scale * g0;
             po[2] = A0;
             po[3] = B0;
-            if (a.flag_out) a.flag_out[f0 + lane] = static_cast<int16_t>(flag);
+            if (a.flag_out) a.flag_out[fo] = static_cast<int16_t>(flag);
         }
         __syncwarp();
     }
@@ -345,8 +358,13 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
     const int leader_lane = lane & ~(G - 1);
     const float inv_scale = 1.0f / a.x_scale;
     int64_t next = 0, end = 0;   // current task [next, end); tasks come from a.counter
+    int64_t n = a.n;
+    if (a.list_n) {
+        const int64_t c = *a.list_n;
+        n = c < n ? c : n;
+    }
 
-    int64_t f = -1;
+    int64_t f = -1, fr = -1;     // task index, frame index
     float yv[PPL];
 #pragma unroll
     for (int j = 0; j < PPL; ++j) yv[j] = 0.f;
@@ -363,17 +381,17 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
     while (true) {
         // ---- hand frames to idle groups (all lanes of a group agree) ----
         unsigned need = __ballot_sync(kFull, gl == 0 && f < 0);
-        while (need != 0 && next < a.n) {
+        while (need != 0 && next < n) {
             if (next >= end) {
                 unsigned long long t = 0;
                 if (lane == 0) t = atomicAdd(a.counter, 1ULL);
                 t = __shfl_sync(kFull, t, 0);
                 next = static_cast<int64_t>(t) * a.task;
-                if (next >= a.n) {
-                    next = end = a.n;
+                if (next >= n) {
+                    next = end = n;
                     break;
                 }
-                end = next + a.task < a.n ? next + a.task : a.n;
+                end = next + a.task < n ? next + a.task : n;
             }
             const int cnt = __popc(need);
             const int64_t avail = end - next;
@@ -389,27 +407,28 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
         if (!__any_sync(kFull, f >= 0)) break;
 
         if (fresh) {
+            fr = a.list ? static_cast<int64_t>(a.list[f]) : f;
             if (a.y) {
-                const float* src = a.y + f * T;
+                const float* src = a.y + fr * T;
 #pragma unroll
                 for (int j = 0; j < PPL; ++j) {
                     const int k = gl + G * j;
                     yv[j] = (k < T) ? src[k] : 0.f;
                 }
             } else {
-                const float* src = a.amps + f * T;
+                const float* src = a.amps + fr * T;
 #pragma unroll
                 for (int j = 0; j < PPL; ++j) {
                     const int k = gl + G * j;
                     yv[j] = (k < T) ? src[k] * iref[k] : 0.f;
                 }
             }
-            const float* q = a.p0 + f * 4;
+            const float* q = a.p0 + fr * 4;
             p[0] = (q[0] - a.x_mid) * inv_scale;
             p[1] = q[1] * inv_scale;
             p[2] = q[2];
             p[3] = q[3];
-            flag = a.flags_in ? (a.flags_in[f] & kInitFlat) : 0;
+            flag = a.flags_in ? (a.flags_in[fr] & kInitFlat) : 0;
             lambda = a.lambda0;
             it = 0;
             st = kMaxIter;
@@ -490,14 +509,15 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
         fresh = false;
         if (f >= 0 && done) {
             if (gl == 0) {
-                float* po = a.params + f * 4;
+                float* po = a.params + fr * 4;
                 po[0] = fmaf(a.x_scale, p[0], a.x_mid);
                 po[1] = a.x_scale * fabsf(p[1]);
                 po[2] = p[2];
                 po[3] = p[3];
-                if (a.rss) a.rss[f] = chi2;
-                if (a.iters) a.iters[f] = static_cast<int16_t>(it);
-                if (a.status) a.status[f] = static_cast<int16_t>(st | flag);
+                if (a.rss) a.rss[fr] = chi2;
+                if (a.iters) a.iters[fr] = static_cast<int16_t>(it + a.iters_base);
+                if (a.status) a.status[fr] = static_cast<int16_t>(st | flag | a.status_or);
+                if (a.fb_list && (st == kMaxIter || st == kSingular)) a.fb_list[atomicAdd(a.fb_count, 1)] = static_cast<int>(fr);
             }
             f = -1;
         }
@@ -612,7 +632,8 @@ cudaError_t launch_fast_readout(const cg_plan_s* p, const int16_t* frames, int64
 }
 
 cudaError_t launch_init(const cg_plan_s* p, const float* y, const float* amps, int64_t n,
-                        float* p0_out, int16_t* flag_out, cudaStream_t s)
+                        float* p0_out, int16_t* flag_out, cudaStream_t s, const int* list,
+                        const int* list_n)
 {
     InitArgs a = p->ia;
     a.n = n;
@@ -620,6 +641,8 @@ cudaError_t launch_init(const cg_plan_s* p, const float* y, const float* amps, i
     a.amps = amps;
     a.p0_out = p0_out;
     a.flag_out = flag_out;
+    a.list = list;
+    a.list_n = list_n;
     const int64_t tasks = (n + 31) / 32;
     const int64_t blocks = (tasks + 3) / 4;
     const int grid = static_cast<int>(blocks < p->grid_init ? blocks : p->grid_init);
@@ -629,7 +652,7 @@ cudaError_t launch_init(const cg_plan_s* p, const float* y, const float* amps, i
 
 cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, int64_t n,
                         const float* p0, const int16_t* flags_in, float* params, float* rss,
-                        int16_t* iters, int16_t* status, cudaStream_t s)
+                        int16_t* iters, int16_t* status, cudaStream_t s, const FitLaunch& fl)
 {
     Fit2Args a{};
     a.n = n;
@@ -642,13 +665,19 @@ cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, i
     a.flags_in = flags_in;
     a.x_mid = static_cast<float>(p->x_mid);
     a.x_scale = static_cast<float>(p->x_scale);
-    a.max_iter = p->opts.max_iter;
+    a.max_iter = fl.max_iter >= 0 ? fl.max_iter : p->opts.max_iter;
     a.tol = static_cast<float>(p->opts.tol);
     a.lambda0 = static_cast<float>(p->opts.lambda0);
     a.params = params;
     a.rss = rss;
     a.iters = iters;
     a.status = status;
+    a.list = fl.list;
+    a.list_n = fl.list_n;
+    a.fb_list = fl.fb_list;
+    a.fb_count = fl.fb_count;
+    a.iters_base = fl.iters_base;
+    a.status_or = fl.status_or;
     a.row_stride = p->T | 1;
     a.counter = p->d.fit_counter;
     a.solve_f64 = p->solve_f64;

@@ -50,8 +50,14 @@ __global__ void __launch_bounds__(128) fit1_kernel(Fit2Args a)
     const float* src_rows = a.y ? a.y : a.amps;
     const bool scale_rows = (a.y == nullptr);
 
+    int64_t n = a.n;
+    if (a.list_n) {
+        const int64_t c = *a.list_n;
+        n = c < n ? c : n;
+    }
     int64_t next = 0, end = 0;      // the warp's current task [next, end)
-    int64_t cur = -1, nxt = -1;     // frame being fit / claimed frame in flight
+    int64_t cur = -1, nxt = -1;     // task being fit / claimed task in flight
+    int64_t cur_f = -1, nxt_f = -1; // their frame indices (list[task] for a frame list)
     int par = 0;                    // cur's slot is par * 32 + lane
     bool fitting = false, fresh = false;
     float q0[4] = {0.f, 1.f, 0.f, 0.f};   // start parameters of nxt
@@ -72,14 +78,14 @@ __global__ void __launch_bounds__(128) fit1_kernel(Fit2Args a)
         int64_t first = 0;
         {
             const unsigned need = __ballot_sync(kFull, nxt < 0);
-            if (need != 0 && next < a.n) {
+            if (need != 0 && next < n) {
                 if (next >= end) {
                     unsigned long long t = 0;
                     if (lane == 0) t = atomicAdd(a.counter, 1ULL);
                     t = __shfl_sync(kFull, t, 0);
                     next = static_cast<int64_t>(t) * a.task;
-                    if (next >= a.n) next = a.n;
-                    end = next + a.task < a.n ? next + a.task : a.n;
+                    if (next >= n) next = n;
+                    end = next + a.task < n ? next + a.task : n;
                 }
                 if (next < end) {
                     const int cnt = __popc(need);
@@ -89,12 +95,13 @@ __global__ void __launch_bounds__(128) fit1_kernel(Fit2Args a)
                     const bool gets = ((need >> lane) & 1u) && rank < take;
                     if (gets) {
                         nxt = next + rank;
-                        const float* q = a.p0 + nxt * 4;
+                        nxt_f = a.list ? static_cast<int64_t>(a.list[nxt]) : nxt;
+                        const float* q = a.p0 + nxt_f * 4;
                         q0[0] = q[0];
                         q0[1] = q[1];
                         q0[2] = q[2];
                         q0[3] = q[3];
-                        qflag = a.flags_in ? (a.flags_in[nxt] & kInitFlat) : 0;
+                        qflag = a.flags_in ? (a.flags_in[nxt_f] & kInitFlat) : 0;
                     }
                     got = __ballot_sync(kFull, gets);
                     first = next;
@@ -106,7 +113,18 @@ __global__ void __launch_bounds__(128) fit1_kernel(Fit2Args a)
         // ---- coalesced asynchronous copy of the claimed rows ----
         dst_of[lane] = ((par ^ 1) * 32 + lane) * TS;
         __syncwarp();
-        if (got != 0) {
+        if (got != 0 && a.list) {
+            // listed frames are not contiguous: one coalesced row per claimer
+            unsigned m = got;
+            while (m != 0) {
+                const int l = __ffs(m) - 1;
+                m &= m - 1;
+                const int64_t rf = __shfl_sync(kFull, nxt_f, l);
+                const float* src = src_rows + rf * T;
+                float* dst = slots + dst_of[l];
+                for (int k = lane; k < T; k += 32) cp_async4(dst + k, src + k);
+            }
+        } else if (got != 0) {
             const float* src = src_rows + first * T;
             const int total = __popc(got) * T;
             int r = lane / T, k = lane - r * T;
@@ -197,14 +215,16 @@ __global__ void __launch_bounds__(128) fit1_kernel(Fit2Args a)
         }
         fresh = false;
         if (fitting && done) {
-            float* po = a.params + cur * 4;
+            float* po = a.params + cur_f * 4;
             po[0] = fmaf(a.x_scale, p[0], a.x_mid);
             po[1] = a.x_scale * fabsf(p[1]);
             po[2] = p[2];
             po[3] = p[3];
-            if (a.rss) a.rss[cur] = chi2;
-            if (a.iters) a.iters[cur] = static_cast<int16_t>(it);
-            if (a.status) a.status[cur] = static_cast<int16_t>(st | flag);
+            if (a.rss) a.rss[cur_f] = chi2;
+            if (a.iters) a.iters[cur_f] = static_cast<int16_t>(it + a.iters_base);
+            if (a.status) a.status[cur_f] = static_cast<int16_t>(st | flag | a.status_or);
+            if (a.fb_list && (st == kMaxIter || st == kSingular))
+                a.fb_list[atomicAdd(a.fb_count, 1)] = static_cast<int>(cur_f);
             fitting = false;
             cur = -1;
         }
@@ -213,6 +233,7 @@ __global__ void __launch_bounds__(128) fit1_kernel(Fit2Args a)
         __syncwarp();
         if (cur < 0 && nxt >= 0) {
             cur = nxt;
+            cur_f = nxt_f;
             nxt = -1;
             par ^= 1;
 #pragma unroll

@@ -76,6 +76,8 @@ struct InitArgs {
     float u_mid, du, span, x_mid, x_scale;
     float* p0_out;           // [n][4] abscissa units
     int16_t* flag_out;       // [n] or null
+    const int* list;         // task i is frame list[i] (fallback pass), or null
+    const int* list_n;       // device count of list entries, or null
 };
 
 // Arguments of the register-resident LM kernel.
@@ -99,7 +101,33 @@ struct Fit2Args {
     float* rss;
     int16_t* iters;
     int16_t* status;
+    // learned-guess polish and its fallback
+    const int* list;         // task i is frame list[i], or null (task i is frame i)
+    const int* list_n;       // device count of list entries (read at start), or null
+    int* fb_list;            // frames that end without converging are appended, or null
+    int* fb_count;
+    int iters_base;          // added to the reported iteration count
+    int status_or;           // OR-ed into the reported status
 };
+
+// Arguments of the learned initial-guess inference kernel (cg_mlp_tc.cu).
+struct MlpArgs {
+    const float* y;          // [n][T] normalised, or null
+    const float* amps;       // [n][T] magnitudes when y is null
+    const float* inv_ref;    // [T]
+    int64_t n;
+    int T, nkb;              // teeth, K blocks of 64 of the first layer
+    const float* tab;        // FP32 tables at the kMlpTab* offsets
+    float x_mid, g_lo, g_hi; // fallback centre; clamp of |g| (abscissa units)
+    float* p0;               // [n][4]
+    int16_t* flags;          // [n] or null
+    int stages;
+    int* err;
+};
+constexpr char kMlpMagic[9] = "CGMLP001";
+constexpr int kMlpHeaderBytes = 24;
+constexpr int kMlpTabB1 = 0, kMlpTabB2 = 256, kMlpTabW3 = 512, kMlpTabB3 = 1536, kMlpTabOutMean = 1540,
+              kMlpTabOutScale = 1544, kMlpTabIn = 1548;
 
 // Arguments of the split-precision DFT-at-teeth GEMM readout.
 struct GemmArgs {
@@ -137,6 +165,11 @@ struct DevTables {
     double* ref_out = nullptr;    // [T]
     int ref_part_rows = 0;
     unsigned long long* fit_counter = nullptr;   // dynamic task counter of the fit kernels
+    void* mlp_W = nullptr;        // [512][256] BF16 weights of the learned guess
+    float* mlp_tab = nullptr;     // its FP32 tables
+    int* fb_list = nullptr;       // [fb_cap] frames left by the polish
+    int* fb_count = nullptr;      // [1]
+    int64_t fb_cap = 0;
 };
 
 }  // namespace cg
@@ -179,6 +212,19 @@ struct cg_plan_s {
     cg::FastArgs fa{};
     cudaStream_t s_read = nullptr, s_fit = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_read = nullptr, ev_join_r = nullptr, ev_join_f = nullptr;
+    // learned initial guess
+    bool mlp_ok = false;
+    CUtensorMap mlp_map{};
+    int mlp_smem = 0;
+    cg::MlpArgs ma{};
+    // per-kernel timing
+    bool timing = false;
+    struct TimedLaunch {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> ev_pool;
 };
 
 namespace cg {
@@ -212,11 +258,28 @@ void* fit1_ptr();   // lane-per-frame LM kernel (cg_fit1.cu)
 size_t fit2_smem(int G, int T);
 cudaError_t launch_fast_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps,
                                 float* y, cudaStream_t s);
+// options of a fit launch beyond the plan's: polish cap, frame list, fallback list
+struct FitLaunch {
+    int max_iter = -1;           // -1: the plan's
+    const int* list = nullptr;
+    const int* list_n = nullptr;
+    int* fb_list = nullptr;
+    int* fb_count = nullptr;
+    int iters_base = 0;
+    int status_or = 0;
+};
 cudaError_t launch_init(const cg_plan_s* p, const float* y, const float* amps, int64_t n,
-                        float* p0_out, int16_t* flag_out, cudaStream_t s);
+                        float* p0_out, int16_t* flag_out, cudaStream_t s, const int* list,
+                        const int* list_n);
 cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, int64_t n,
                         const float* p0, const int16_t* flags_in, float* params, float* rss,
-                        int16_t* iters, int16_t* status, cudaStream_t s);
+                        int16_t* iters, int16_t* status, cudaStream_t s,
+                        const FitLaunch& fl = FitLaunch());
+
+// learned initial guess (cg_mlp_tc.cu)
+cudaError_t setup_mlp(cg_plan_s* p, const unsigned char* blob, size_t bytes, const char** why);
+cudaError_t launch_mlp(const cg_plan_s* p, const float* y, const float* amps, int64_t n, float* p0,
+                       int16_t* flags, cudaStream_t s);
 
 // split-precision GEMM readout (cg_gemm.cu)
 cudaError_t setup_gemm(cg_plan_s* p);

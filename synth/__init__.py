@@ -120,21 +120,26 @@ def lineshape(x: np.ndarray, c: np.ndarray, fwhm: np.ndarray | float,
 
 
 def frames(stream: Stream, n_frames: int, *, first_frame: int = 0, cavity: bool = True,
-           center_amp_hz: float = 5e6, drive_hz: float = DRIVE_HZ, fwhm_hz: float = FWHM_HZ,
-           depth: float = 0.7, shape: str = "dip", sigma: float | None = None,
-           snr_db: float | None = None, noise_stream: int = 0, device=None) -> dict:
+           center_amp_hz: float = 5e6, drive_hz: float = DRIVE_HZ, fwhm_hz=FWHM_HZ,
+           depth: float = 0.7, shape: str = "dip", sigma=None,
+           snr_db=None, noise_stream: int = 0, centers=None, device=None) -> dict:
     """Synthesise ``n_frames`` int16 frames [n_frames, N] (see the module recipe).
 
-    ``device`` = None / "cpu" uses numpy; a torch CUDA device builds the frames
-    there with torch (for the largest workloads).  Returns dict(frames, centers)."""
+    ``centers`` (per frame, Hz) replaces the sinusoidal drive; ``fwhm_hz``,
+    ``sigma`` and ``snr_db`` may be per-frame arrays.  ``device`` = None / "cpu"
+    uses numpy; a torch CUDA device builds the frames there with torch (for the
+    largest workloads).  Returns dict(frames, centers)."""
     g = stream.geom
     N, T, fs = g.frame_len, g.n_teeth, g.sample_rate
     if sigma is None:
-        sigma = 0.0 if snr_db is None else RMS_TARGET / 10.0 ** (snr_db / 20.0)
+        sigma = 0.0 if snr_db is None else RMS_TARGET / 10.0 ** (np.asarray(snr_db, dtype=np.float64) / 20.0)
+    sigma = np.asarray(sigma, dtype=np.float64)
     E = RMS_TARGET * math.sqrt(2.0 / T)
     idx = np.arange(first_frame, first_frame + n_frames, dtype=np.int64)
     t0 = idx.astype(np.float64) * N / fs
-    centers = center_amp_hz * np.sin(2.0 * math.pi * drive_hz * t0)
+    if centers is None:
+        centers = center_amp_hz * np.sin(2.0 * math.pi * drive_hz * t0)
+    centers = np.asarray(centers, dtype=np.float64)
     if cavity:
         shape_f = lineshape(g.tooth_x, centers, fwhm_hz, depth, shape)
     else:
@@ -152,9 +157,9 @@ def frames(stream: Stream, n_frames: int, *, first_frame: int = 0, cavity: bool 
         for s in range(0, n_frames, CHUNK):
             e = min(n_frames, s + CHUNK)
             sig = ac[s:e] @ Cb - asn[s:e] @ Sb
-            if sigma > 0:
-                sig += sigma * _chunk_noise(stream.seed, noise_stream, first_frame + s,
-                                            e - s, N)
+            if np.any(sigma > 0):
+                sg = sigma[s:e, None] if sigma.ndim else sigma
+                sig += sg * _chunk_noise(stream.seed, noise_stream, first_frame + s, e - s, N)
             out[s:e] = np.clip(np.rint(sig), -FULL_SCALE, FULL_SCALE - 1).astype(np.int16)
     return dict(frames=out, centers=centers)
 
@@ -191,10 +196,22 @@ def _frames_torch(ac, asn, Cb, Sb, sigma, seed, noise_stream, first_frame, devic
         a1 = torch.from_numpy(ac[s:e].astype(np.float32)).to(dev)
         a2 = torch.from_numpy(asn[s:e].astype(np.float32)).to(dev)
         sig = a1 @ Ct - a2 @ St
-        if sigma > 0:
-            sig += sigma * torch.randn(sig.shape, generator=gen, device=dev)
+        if np.any(sigma > 0):
+            sg = (torch.from_numpy(sigma[s:e].astype(np.float32)).to(dev)[:, None] if sigma.ndim
+                  else float(sigma))
+            sig += sg * torch.randn(sig.shape, generator=gen, device=dev)
         out[s:e] = torch.clamp(torch.round(sig), -FULL_SCALE, FULL_SCALE - 1).to(torch.int16)
     return out
+
+
+def learned_params(n: int, *, seed: int, center_range_hz=100e6, fwhm_range_hz=(60e6, 100e6),
+                   snr_range_db=(20.0, 40.0)) -> dict:
+    """Per-frame cavity parameters of the learned-guess workload: centre
+    U(-range, range), FWHM U(lo, hi), time-domain SNR U(lo, hi) dB."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x1EA4]))
+    return dict(c=rng.uniform(-center_range_hz, center_range_hz, n),
+                fwhm=rng.uniform(fwhm_range_hz[0], fwhm_range_hz[1], n),
+                snr_db=rng.uniform(snr_range_db[0], snr_range_db[1], n))
 
 
 def tooth_domain_spectra(geom: Geometry, n: int, *, seed: int, center_range_hz=100e6,

@@ -1,0 +1,165 @@
+"""Learned initial guess on the GPU against the FP64 network reference (GPU).
+
+Training kernels (FP32): forward, loss, every gradient block and one Adam
+step are compared with oracle/mlp.py on the same parameters and data;
+training is deterministic and lowers the loss.  Inference kernel (tcgen05,
+BF16 operands, FP32 accumulation): compared with the reference evaluated on
+the same BF16-rounded operands (input, W1, the first hidden layer, W2), so
+the remaining difference is accumulation order and the hardware tanh.
+Pipeline: with a network whose guess never converges in the polish steps,
+every frame falls back to the full LM from the moment guess and must then
+match the moment-guess plan bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2307_12988_gb300 as cg
+import synth
+from oracle import mlp as omlp
+from tests import workloads
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+def _blocks(n_in, H, n_out):
+    sizes = [H * n_in, H, H * H, H, n_out * H, n_out]
+    names = ["W1", "b1", "W2", "b2", "W3", "b3"]
+    offs = np.cumsum([0] + sizes)
+    return [(names[i], offs[i], offs[i + 1]) for i in range(6)]
+
+
+@pytest.mark.parametrize("shape,n", [((221, 256, 4), 300), ((21, 64, 4), 77), ((99, 256, 4), 4096)])
+def test_forward_loss_gradient_match_oracle(shape, n):
+    n_in, H, n_out = shape
+    net = cg.Mlp(n_in, H, n_out, max_batch=4096, seed=7)
+    theta = net.params().astype(np.float64)
+    # biases nonzero so every block is exercised
+    rng = np.random.default_rng(1)
+    for name, a, b in _blocks(n_in, H, n_out):
+        if name.startswith("b"):
+            theta[a:b] = rng.normal(0, 0.3, b - a)
+    net.set_params(theta.astype(np.float32))
+    theta = net.params().astype(np.float64)
+    x = rng.normal(0, 1, (n, n_in)).astype(np.float32)
+    t = rng.normal(0, 1, (n, n_out)).astype(np.float32)
+    xd, td = _dev(x), _dev(t)
+    out = net.forward(xd).cpu().numpy().astype(np.float64)
+    want = omlp.forward(theta, x.astype(np.float64), n_in, H, n_out)
+    assert np.max(np.abs(out - want)) <= 1e-5 * max(1.0, np.max(np.abs(want)))
+    loss, grad = net.backward(xd, td)
+    torch.cuda.synchronize()
+    L, g = omlp.loss_and_grad(theta, x.astype(np.float64), t.astype(np.float64), n_in, H, n_out)
+    assert abs(loss.item() - L) <= 1e-5 * L
+    grad = grad.cpu().numpy().astype(np.float64)
+    for name, a, b in _blocks(n_in, H, n_out):
+        scale = np.max(np.abs(g[a:b]))
+        err = np.max(np.abs(grad[a:b] - g[a:b]))
+        assert err <= 1e-4 * scale, (name, err, scale)
+    # one Adam step from zero moments
+    net.adam(1e-3)
+    new = net.params().astype(np.float64)
+    want_new, _, _ = omlp.adam_step(theta, grad, np.zeros_like(theta), np.zeros_like(theta), 1, 1e-3)
+    assert np.max(np.abs(new - want_new)) <= 2e-7 + 1e-6 * np.max(np.abs(theta))
+
+
+def test_training_is_deterministic_and_learns():
+    n_in, H, n_out, n = 64, 128, 4, 8192
+    rng = np.random.default_rng(2)
+    A = rng.normal(0, 1, (n_in, n_out)) / math.sqrt(n_in)
+    x = rng.normal(0, 1, (n, n_in)).astype(np.float32)
+    t = np.tanh(x @ A * 2.0).astype(np.float32)
+    xd, td = _dev(x), _dev(t)
+    perm = _dev(rng.permutation(n).astype(np.int32), torch.int32)
+    runs = []
+    for _ in range(2):
+        net = cg.Mlp(n_in, H, n_out, max_batch=512, seed=3)
+        first = None
+        for epoch in range(6):
+            losses = net.train_epoch(xd, td, perm, 256, 2e-3).cpu().numpy()
+            first = losses[0] if first is None else first
+        runs.append((net.params(), losses[-1], first))
+        net.close()
+    assert np.array_equal(runs[0][0], runs[1][0]), "training is not deterministic"
+    assert runs[0][1] < 0.1 * runs[0][2], (runs[0][1], runs[0][2])
+
+
+def _plan(geom, **opts):
+    return cg.Plan(geom.sample_rate, geom.frame_len, geom.tooth_freqs, geom.tooth_x, None, **opts)
+
+
+def _net_blob(n_in, seed, in_mean, in_scale, out_mean, out_scale, zero=False):
+    net = cg.Mlp(n_in, 256, 4, max_batch=256, seed=seed)
+    if zero:
+        net.set_params(np.zeros(net.n_params, dtype=np.float32))
+    net.set_norm(in_mean, in_scale, out_mean, out_scale)
+    theta = net.params().astype(np.float64)
+    blob = net.save()
+    net.close()
+    return blob, theta
+
+
+@pytest.mark.parametrize("geom,n", [(synth.WIDE, 300), (synth.TINY, 129), (synth.PAPER_RATE, 1000)])
+def test_inference_kernel_matches_rounded_oracle(geom, n):
+    T = geom.n_teeth
+    d = synth.tooth_domain_spectra(geom, n, seed=42)
+    y = d["y"].astype(np.float32)
+    in_mean = y.mean(axis=0).astype(np.float32)
+    in_scale = (1.0 / y.std(axis=0)).astype(np.float32)
+    out_mean = np.array([0.0, 40e6, -0.7, 1.0], dtype=np.float32)
+    out_scale = np.array([5e7, 1e7, 0.1, 0.05], dtype=np.float32)
+    blob, theta = _net_blob(T, 5, in_mean, in_scale, out_mean, out_scale)
+    with _plan(geom, init=cg.INIT_MLP) as plan:
+        plan.mlp_load(blob)
+        p0 = plan.mlp_infer(_dev(y)).cpu().numpy().astype(np.float64)
+    xs = ((y - in_mean) * in_scale).astype(np.float32).astype(np.float64)   # FP32 like the kernel
+    o = omlp.forward(theta, xs, T, 256, 4, operand_round=omlp.bf16_round)
+    want = o * out_scale + out_mean
+    x_scale = np.mean(np.diff(geom.tooth_x))
+    want[:, 1] = np.clip(np.abs(want[:, 1]), 0.5 * x_scale, 0.5 * (T - 1) * x_scale)
+    # in the network's standardised output units
+    err = np.max(np.abs((p0 - want) / out_scale))
+    assert err <= 2e-3 * max(1.0, np.max(np.abs(o))), err
+
+
+def test_mlp_plan_errors():
+    g = synth.WIDE
+    with _plan(g, init=cg.INIT_MLP) as plan:
+        frames = torch.zeros((4, g.frame_len), dtype=torch.int16, device=DEV)
+        with pytest.raises(cg.CgError, match="CG_ERR_STATE"):
+            plan.process(frames)
+        with pytest.raises(cg.CgError, match="CG_ERR_ARG"):
+            plan.mlp_load(b"not a network")
+        blob, _ = _net_blob(20, 1, np.zeros(20), np.ones(20), np.zeros(4), np.ones(4))
+        with pytest.raises(cg.CgError, match="shape"):
+            plan.mlp_load(blob)
+
+
+def test_all_frames_fall_back_to_the_moment_path_bit_exactly():
+    w = workloads.workload("wide")
+    g = w["geom"]
+    frames = _dev(w["frames"], torch.int16)
+    args = workloads.plan_args(w)
+    with cg.Plan(*args) as ref_plan:
+        ref = ref_plan.process(frames)
+    # a network whose guess is a far, narrow, zero-offset dip: one polish
+    # step cannot converge, so every frame takes the fallback
+    T = g.n_teeth
+    blob, _ = _net_blob(T, 1, np.zeros(T), np.ones(T), np.array([900e6, 5e6, 0.5, 0.0]), np.ones(4), zero=True)
+    with cg.Plan(*args, init=cg.INIT_MLP, polish_iter=1) as plan:
+        plan.mlp_load(blob)
+        got = plan.process(frames)
+        cg.cg_check_device(plan.handle)
+    st = got["status"].cpu().numpy()
+    assert np.all(st & cg.FIT_FALLBACK), "some frame did not fall back"
+    assert np.array_equal(st & ~cg.FIT_FALLBACK, ref["status"].cpu().numpy())
+    assert np.array_equal(got["iters"].cpu().numpy(), ref["iters"].cpu().numpy() + 1)
+    for k in ("params", "rss", "amps", "y"):
+        assert torch.equal(got[k], ref[k]), k
