@@ -107,6 +107,9 @@ def _dist():
 GEOMETRIES = {
     # name: (synth geometry attribute, generator keywords)
     "paper_rate": ("PAPER_RATE", dict(snr_db=30.0, center_amp_hz=20e6)),
+    # the learned-guess workload: per-frame centre U(+-100 MHz), FWHM U(60, 100) MHz,
+    # SNR U(20, 40) dB on the wide geometry (held out from the network's training)
+    "learned": ("WIDE", dict(learned=True)),
     "wide": ("WIDE", dict(snr_db=30.0, center_amp_hz=20e6)),
     "tiny": ("TINY", dict(sigma=0.01 * 2048, center_amp_hz=5e6)),
     "serve4096": ("SERVE_4096", dict(snr_db=30.0, center_amp_hz=20e6)),
@@ -127,12 +130,55 @@ def geometry(args):
 def build_workload(args, n_frames, n_ref, device, seed_offset=0):
     import synth
     g = geometry(args)
-    kw = GEOMETRIES[args.workload][1]
+    kw = dict(GEOMETRIES[args.workload][1])
     stream = synth.make_stream(g, synth.BASE_SEED + 2 + seed_offset)
+    if kw.pop("learned", False):
+        lp = synth.learned_params(n_frames, seed=synth.BASE_SEED + 600 + seed_offset)
+        kw = dict(centers=lp["c"], fwhm_hz=lp["fwhm"], snr_db=lp["snr_db"])
+        noise = dict(snr_db=30.0)
+    else:
+        noise = {k: v for k, v in kw.items() if k in ("snr_db", "sigma")}
     fr = synth.frames(stream, n_frames, device=device, **kw)
-    noise = {k: v for k, v in kw.items() if k in ("snr_db", "sigma")}
     rf = synth.frames(stream, n_ref, cavity=False, noise_stream=1, device=device, **noise)
     return g, fr["frames"], rf["frames"]
+
+
+MLP_BLOB = os.path.join(ROOT, "paper_2307_12988_gb300", "data", "mlp_wide_t221.cgmlp")
+
+# FP32 operations of one LM point evaluation (model, residual, Jacobian and
+# the 14 running sums of J^T J, J^T r and chi^2): 11 + 10 FMA x 2 + 4 adds
+LM_FLOP_PER_POINT = 35
+
+
+def kernel_rooflines(stage_ms, stage_launches, n, g, T, args, mean_iters, hbm, bf16):
+    """Per-kernel figures from the timing pass: mean launch time and the
+    roofline each is bound by (algorithmic work / launch time)."""
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12       # FP32 FMA lanes x 2 flop x max SM clock, TFLOP/s
+    out = {}
+    for st, ms in stage_ms.items():
+        cnt = stage_launches[st]
+        per = ms / cnt / 1e3                       # s per launch
+        frames = n * args.steps_timed / cnt
+        r = {"launches": cnt, "ms_per_launch": per * 1e3}
+        if st == "readout" and args.readout == "fft":
+            b = (2 * g.frame_len + 4 * T) * frames
+            r.update(bound="hbm", achieved=b / per / 1e9, peak=hbm, unit="GB/s")
+        elif st == "readout":
+            f = 2.0 * g.frame_len * 2 * T * frames
+            r.update(bound="tensor", achieved=f / per / 1e12, peak=bf16, unit="TFLOP/s")
+        elif st == "init":
+            b = (4 * T + 16 + 2) * frames
+            r.update(bound="hbm", achieved=b / per / 1e9, peak=hbm, unit="GB/s")
+        elif st == "mlp":
+            f = 2.0 * (T * 256 + 256 * 256) * frames
+            r.update(bound="tensor", achieved=f / per / 1e12, peak=bf16, unit="TFLOP/s")
+        elif st == "fit":
+            f = LM_FLOP_PER_POINT * T * (mean_iters + 1.0) * frames
+            r.update(bound="alu", achieved=f / per / 1e12, peak=alu_peak, unit="TFLOP/s")
+        if "achieved" in r:
+            r["frac"] = r["achieved"] / r["peak"]
+        out[st] = r
+    return out
 
 
 def cpu_baseline_leg(frames, params, status, iters, plan, ref, g, args) -> dict:
@@ -170,15 +216,6 @@ def cpu_baseline_leg(frames, params, status, iters, plan, ref, g, args) -> dict:
     return {"cpu_baseline": cpu, "fit_error": fe}
 
 
-def launches_per_step(plan, n) -> int:
-    """Kernels of this library that one cg_process call launches."""
-    path = plan.info["path"]
-    if path == 3:   # pipeline: readout, initial guess and fit kernels per chunk
-        chunk = plan._opts.chunk_frames or n
-        return 3 * ((n + chunk - 1) // chunk)
-    return 1 if path == 1 else 2
-
-
 def run_ours(args):
     import torch
     import paper_2307_12988_gb300 as cg
@@ -198,7 +235,12 @@ def run_ours(args):
     plan = cg.Plan(g.sample_rate, g.frame_len, g.tooth_freqs, g.tooth_x, ref,
                    lanes_per_frame=args.lanes, path=args.path, chunk_frames=args.chunk,
                    readout=(cg.READOUT_GEMM_SPLIT if args.readout == "gemm" else cg.READOUT_FFT),
-                   sample_bits=args.sample_bits)
+                   sample_bits=args.sample_bits,
+                   init=(cg.INIT_MLP if args.init == "mlp" else cg.INIT_MOMENT),
+                   polish_iter=args.polish)
+    if args.init == "mlp":
+        with open(MLP_BLOB, "rb") as f:
+            plan.mlp_load(f.read())
     T = plan.T
     amps = torch.empty((n, T), dtype=torch.float32, device=dev)
     params = torch.empty((n, 4), dtype=torch.float32, device=dev)
@@ -236,8 +278,23 @@ def run_ours(args):
         ms = float(t.item())
     ms_step = ms / args.steps
 
-    hbm, _, peak_kind = _peaks()
+    # per-kernel timing pass (events on the launching streams), after the
+    # timed region so that it does not disturb the step time
+    plan.timing(True)
+    args.steps_timed = max(1, min(args.steps, 20))
+    for _ in range(args.steps_timed):
+        step()
+    torch.cuda.synchronize()
+    stages = plan.timing_collect()
+    plan.timing(False)
+    mean_iters = float(iters.float().mean().item())
+
+    hbm, bf16, peak_kind = _peaks()
     bytes_per_frame = 2 * g.frame_len + 4 * T + 16 + 4 + 2 + 2
+    kern = kernel_rooflines({k: v[0] for k, v in stages.items()}, {k: v[1] for k, v in stages.items()},
+                            n, g, T, args, mean_iters, hbm, bf16)
+    dominant = max(kern, key=lambda k: kern[k]["launches"] * kern[k]["ms_per_launch"])
+    dom = kern[dominant]
     total_frames = n * ws
     value = total_frames / (ms_step / 1e3)
     achieved = bytes_per_frame * n / (ms_step / 1e3) / 1e9
@@ -249,16 +306,20 @@ def run_ours(args):
         "config": {"workload": workload_name(args, n),
                    "frames_per_gpu": n, "frame_len": g.frame_len, "teeth": T,
                    "sample_rate_hz": g.sample_rate, "resident_bytes": 2 * g.frame_len * n,
-                   "l2": "inputs (2.2 GB) larger than L2; no flush",
+                   "l2": f"inputs ({2 * g.frame_len * n / 1e9:.1f} GB) larger than L2; no flush",
                    "lanes_per_frame": plan.info["lanes_per_frame"],
                    "path": ["auto", "fused", "split", "pipeline"][plan.info["path"]],
-                   "fft_len": plan.info["fft_len"]},
+                   "fft_len": plan.info["fft_len"], "readout": args.readout, "init": args.init,
+                   "polish_iter": args.polish if args.init == "mlp" else None},
         "input_gbs": total_frames * 2 * g.frame_len / (ms_step / 1e3) / 1e9,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
-                     "peak_kind": peak_kind,
+        "roofline": {"kernel": dominant, "bound": dom.get("bound"), "achieved": dom.get("achieved"),
+                     "peak": dom.get("peak"), "unit": dom.get("unit"), "frac": dom.get("frac"),
+                     "traffic": None, "peak_kind": peak_kind},
+        "step_hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "algorithmic_bytes_per_frame": bytes_per_frame},
-        "gpu_launches": args.steps * launches_per_step(plan, n),
+        "kernels": kern,
+        "mean_iters": mean_iters,
+        "gpu_launches": int(round(sum(v[1] for v in stages.values()) * args.steps / args.steps_timed)),
         "clocks": clocks,
     }
     torch.cuda.synchronize()
@@ -382,6 +443,9 @@ def main():
     ap.add_argument("--chunk", type=int, default=0, help="frames per pipelined chunk (0: default)")
     ap.add_argument("--workload", choices=sorted(GEOMETRIES), default="paper_rate")
     ap.add_argument("--readout", choices=["fft", "gemm"], default="fft")
+    ap.add_argument("--init", choices=["moment", "mlp"], default="moment",
+                    help="initial guess; mlp loads the trained network (221 teeth)")
+    ap.add_argument("--polish", type=int, default=0, help="LM polish steps after the MLP guess (0: 2)")
     ap.add_argument("--sample-bits", type=int, default=12,
                     help="declared sample range for the GEMM readout (the workloads are 12-bit)")
     ap.add_argument("--quick", action="store_true", help="skip fit check, CPU baseline and e2e")

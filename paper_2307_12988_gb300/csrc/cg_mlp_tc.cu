@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(160, 1) mlp_infer_kernel(const __grid_constant
     unsigned char* Abuf = sm;
     unsigned char* Wst = sm + kABytes;
     const int S = a.stages;
-    uint64_t* full = reinterpret_cast<uint64_t*>(Wst + S * kChunkBytes);
+    float* tab = reinterpret_cast<float*>(Wst + S * kChunkBytes);   // FP32 tables, staged
+    uint64_t* full = reinterpret_cast<uint64_t*>(tab + kMlpTabIn + 2 * a.T);
     uint64_t* empty = full + kStagesMax;
     uint64_t* done = empty + kStagesMax;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
@@ -88,8 +89,8 @@ __global__ void __launch_bounds__(160, 1) mlp_infer_kernel(const __grid_constant
     const int T = a.T, nkb = a.nkb;
     const int n1 = 2 * nkb;      // layer-1 chunks (K blocks x 2 row halves)
     const int nch = n1 + 8;      // + layer-2 chunks
-    const float* tab = a.tab;
     const bool issuer = (warp == 4 && lane == 0);
+    for (int i = tid; i < kMlpTabIn + 2 * T; i += blockDim.x) tab[i] = a.tab[i];
 
     if (issuer) {
         for (int s = 0; s < S; ++s) {
@@ -161,17 +162,29 @@ __global__ void __launch_bounds__(160, 1) mlp_infer_kernel(const __grid_constant
         const float* src = (a.y ? a.y : a.amps) + f0 * T;
         const float* in_mean = tab + kMlpTabIn;
         const float* in_scale = in_mean + T;
+        // the tile's rows are contiguous: one flat coalesced sweep with eight
+        // loads in flight per thread, (row, tooth) tracked incrementally
         const int total = rows * T;
         int row = tid / T, k = tid - (tid / T) * T;
-        for (int e = tid; e < total; e += kMM) {
-            float v = src[e];
-            if (!a.y) v *= a.inv_ref[k];
-            *reinterpret_cast<__nv_bfloat16*>(Abuf + a_off(row, k)) =
-                __float2bfloat16_rn((v - in_mean[k]) * in_scale[k]);
-            k += kMM;
-            while (k >= T) {
-                k -= T;
-                ++row;
+        for (int e0 = 0; e0 < total; e0 += 8 * kMM) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = e0 + q * kMM + tid;
+                v[q] = e < total ? __ldcs(src + e) : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (e0 + q * kMM + tid < total) {
+                    float x = a.y ? v[q] : v[q] * __ldg(a.inv_ref + k);
+                    x = (x - in_mean[k]) * in_scale[k];
+                    *reinterpret_cast<__nv_bfloat16*>(Abuf + a_off(row, k)) = __float2bfloat16_rn(x);
+                }
+                k += kMM;
+                while (k >= T) {
+                    k -= T;
+                    ++row;
+                }
             }
         }
         const int kpad = nkb * 64;
@@ -302,7 +315,10 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
 
 }  // namespace
 
-int mlp_smem_bytes(int stages) { return 1024 + kABytes + stages * kChunkBytes + 8 * (2 * kStagesMax + 1) + 16; }
+int mlp_smem_bytes(int stages, int T)
+{
+    return 1024 + kABytes + stages * kChunkBytes + 4 * (kMlpTabIn + 2 * T) + 8 * (2 * kStagesMax + 1) + 16;
+}
 
 // Parses a cg_mlp_save blob, packs the BF16 weight matrix, the FP32 tables and
 // the tensor map into the plan.
@@ -407,7 +423,7 @@ cudaError_t setup_mlp(cg_plan_s* p, const unsigned char* blob, size_t bytes, con
     m.g_hi = static_cast<float>(0.5 * (p->T - 1) * p->x_scale);
     m.stages = 2;
     m.err = p->d.err;
-    p->mlp_smem = mlp_smem_bytes(m.stages);
+    p->mlp_smem = mlp_smem_bytes(m.stages, p->T);
     if ((e = cudaFuncSetAttribute(reinterpret_cast<void*>(&mlp_infer_kernel),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, p->mlp_smem)) != cudaSuccess)
         return e;
