@@ -9,8 +9,10 @@
 // S-stage mbarrier ring.  The spectra and then a1 are written by the threads
 // into the K-major 128-byte-swizzled layout the MMA reads; the 256 hidden
 // activations of a row live in 256 TMEM columns.
-//   warps 0-3: stage the input tile, run both epilogues (TMEM lane = row);
-//   warp 4:    owns TMEM; one lane issues the TMA loads and tcgen05.mma.
+//   warps 0-7: stage the input tile and run both epilogues; warp w reads
+//              TMEM lanes 32 (w % 4).. (rows) and column half w / 4, so the
+//              second epilogue of half 0 overlaps the layer-2 MMAs of half 1;
+//   warp 8:    owns TMEM; one lane issues the TMA loads and tcgen05.mma.
 // Every wait is bounded; on time-out the block records an error, stops
 // issuing, drains its loads and frees its TMEM.
 #include <cmath>
@@ -36,6 +38,8 @@ constexpr int kChunkRows = 128;                 // weight rows per chunk (MMA N)
 constexpr int kChunkBytes = kChunkRows * 64 * 2;
 constexpr int kABytes = 4 * kMM * 64 * 2;       // A operand: 4 K blocks of 64
 constexpr int kStagesMax = 4;
+constexpr int kEpiWarps = 8;                    // staging + epilogue warps (2 per TMEM lane quarter)
+constexpr int kMlpThreads = (kEpiWarps + 1) * 32;  // + the TMA / MMA issuing warp
 constexpr uint32_t kPolls = 1u << 22;
 
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag)
@@ -69,7 +73,7 @@ __device__ __forceinline__ uint32_t a_off(int row, int k)
                                  ((kl & 7) << 1));
 }
 
-__global__ void __launch_bounds__(160, 1) mlp_infer_kernel(const __grid_constant__ CUtensorMap tmW, MlpArgs a)
+__global__ void __launch_bounds__(kMlpThreads, 2) mlp_infer_kernel(const __grid_constant__ CUtensorMap tmW, MlpArgs a)
 {
     extern __shared__ __align__(1024) unsigned char msm_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
@@ -77,19 +81,20 @@ __global__ void __launch_bounds__(160, 1) mlp_infer_kernel(const __grid_constant
     unsigned char* Abuf = sm;
     unsigned char* Wst = sm + kABytes;
     const int S = a.stages;
+    const int T = a.T, nkb = a.nkb;
     float* tab = reinterpret_cast<float*>(Wst + S * kChunkBytes);   // FP32 tables, staged
-    uint64_t* full = reinterpret_cast<uint64_t*>(tab + kMlpTabIn + 2 * a.T);
+    float* red = tab + kMlpTabIn + 2 * T;                            // [128][4] output partials
+    uint64_t* full = reinterpret_cast<uint64_t*>(red + kMM * 4);
     uint64_t* empty = full + kStagesMax;
-    uint64_t* done = empty + kStagesMax;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* done = empty + kStagesMax;                             // [2]: one per column half
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t f0 = static_cast<int64_t>(blockIdx.x) * kMM;
-    const int T = a.T, nkb = a.nkb;
-    const int n1 = 2 * nkb;      // layer-1 chunks (K blocks x 2 row halves)
+    const int n1 = 2 * nkb;      // layer-1 chunks: column half-major, K blocks within
     const int nch = n1 + 8;      // + layer-2 chunks
-    const bool issuer = (warp == 4 && lane == 0);
+    const bool issuer = (warp == kEpiWarps && lane == 0);
     for (int i = tid; i < kMlpTabIn + 2 * T; i += blockDim.x) tab[i] = a.tab[i];
 
     if (issuer) {
@@ -97,26 +102,34 @@ __global__ void __launch_bounds__(160, 1) mlp_infer_kernel(const __grid_constant
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        tc::mbar_init(done, 1);
+        tc::mbar_init(&done[0], 1);
+        tc::mbar_init(&done[1], 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
         tc::prefetch_tmap(&tmW);
     }
-    if (warp == 4) tc::tmem_alloc(tmem_slot, kHid);
+    if (warp == kEpiWarps) tc::tmem_alloc(tmem_slot, kHid);
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
+    // chunk g -> layer, column half and K block
+    auto chunk_geom = [&](int g, int& layer, int& nh, int& kb) {
+        const int per = g < n1 ? nkb : 4;
+        const int h = g < n1 ? g : g - n1;
+        layer = g < n1 ? 0 : 1;
+        nh = h / per;
+        kb = h - nh * per;
+    };
     // issuer state
     int issued = 0, consumed = 0;
     auto load_chunk = [&](int g) {
+        int layer, nh, kb;
+        chunk_geom(g, layer, nh, kb);
         const int s = g % S;
-        const int h = g < n1 ? g : g - n1;
-        const int x = (h >> 1) * 64;
-        const int y = (g < n1 ? 0 : kHid) + (h & 1) * kChunkRows;
         tc::mbar_arrive_expect_tx(&full[s], kChunkBytes);
-        tc::tma_load_2d(Wst + s * kChunkBytes, &tmW, x, y, &full[s]);
+        tc::tma_load_2d(Wst + s * kChunkBytes, &tmW, kb * 64, layer * kHid + nh * kChunkRows, &full[s]);
     };
     // chunk q's stage takes chunk q + S once q's MMAs have read it
     auto refill = [&](int q) -> bool {
@@ -133,8 +146,8 @@ __global__ void __launch_bounds__(160, 1) mlp_infer_kernel(const __grid_constant
             if (!wait_or_abort(&full[s], (g / S) & 1u, abort_flag)) return false;
             consumed = g + 1;
             tc::tc_fence_after();
-            const int h = g < n1 ? g : g - n1;
-            const int kb = h >> 1, nh = h & 1;
+            int layer, nh, kb;
+            chunk_geom(g, layer, nh, kb);
             const uint32_t sa = tc::smem_u32(Abuf) + kb * (kMM * 128);
             const uint32_t sb = tc::smem_u32(Wst + s * kChunkBytes);
             const uint32_t d = tmem + static_cast<uint32_t>(nh * kChunkRows);
@@ -150,13 +163,27 @@ __global__ void __launch_bounds__(160, 1) mlp_infer_kernel(const __grid_constant
         }
         return true;
     };
+    // one layer: column half 0, commit, column half 1, commit (the epilogue
+    // of half 0 overlaps the MMAs of half 1); always commits, so that the
+    // waiting warps are released also after an abort
+    auto run_layer = [&](int g0, int per) {
+        if (!*abort_flag && !run_chunks(g0, g0 + per)) *abort_flag = 1;
+        tc::mma_commit(&done[0]);
+        if (!*abort_flag && !run_chunks(g0 + per, g0 + 2 * per)) *abort_flag = 1;
+        tc::mma_commit(&done[1]);
+    };
 
     if (issuer) {
         for (; issued < S && issued < nch; ++issued) load_chunk(issued);
     }
 
+    // epilogue warps: TMEM lane quarter (rows) and column half
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
+
     // ---- stage the input tile: (y - in_mean) * in_scale -> BF16 ----
-    if (warp < 4) {
+    if (warp < kEpiWarps) {
         const int64_t left = a.n - f0;
         const int rows = left < kMM ? static_cast<int>(left) : kMM;
         const float* src = (a.y ? a.y : a.amps) + f0 * T;
@@ -164,56 +191,57 @@ __global__ void __launch_bounds__(160, 1) mlp_infer_kernel(const __grid_constant
         const float* in_scale = in_mean + T;
         // the tile's rows are contiguous: one flat coalesced sweep with eight
         // loads in flight per thread, (row, tooth) tracked incrementally
+        constexpr int kE = kEpiWarps * 32;
         const int total = rows * T;
-        int row = tid / T, k = tid - (tid / T) * T;
-        for (int e0 = 0; e0 < total; e0 += 8 * kMM) {
+        int r = tid / T, k = tid - (tid / T) * T;
+        for (int e0 = 0; e0 < total; e0 += 8 * kE) {
             float v[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const int e = e0 + q * kMM + tid;
+                const int e = e0 + q * kE + tid;
                 v[q] = e < total ? __ldcs(src + e) : 0.f;
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                if (e0 + q * kMM + tid < total) {
+                if (e0 + q * kE + tid < total) {
                     float x = a.y ? v[q] : v[q] * __ldg(a.inv_ref + k);
                     x = (x - in_mean[k]) * in_scale[k];
-                    *reinterpret_cast<__nv_bfloat16*>(Abuf + a_off(row, k)) = __float2bfloat16_rn(x);
+                    *reinterpret_cast<__nv_bfloat16*>(Abuf + a_off(r, k)) = __float2bfloat16_rn(x);
                 }
-                k += kMM;
+                k += kE;
                 while (k >= T) {
                     k -= T;
-                    ++row;
+                    ++r;
                 }
             }
         }
+        // K padding of every row and the rows past the end: zeros
         const int kpad = nkb * 64;
-        if (tid >= rows) {
-            for (int k2 = 0; k2 < kpad; k2 += 8)
-                *reinterpret_cast<uint4*>(Abuf + a_off(tid, k2)) = make_uint4(0u, 0u, 0u, 0u);
-        } else {
-            for (int k2 = T; k2 < kpad; ++k2)
-                *reinterpret_cast<__nv_bfloat16*>(Abuf + a_off(tid, k2)) = __float2bfloat16_rn(0.f);
+        if (half == 0) {
+            if (row >= rows) {
+                for (int k2 = 0; k2 < kpad; k2 += 8)
+                    *reinterpret_cast<uint4*>(Abuf + a_off(row, k2)) = make_uint4(0u, 0u, 0u, 0u);
+            } else {
+                for (int k2 = T; k2 < kpad; ++k2)
+                    *reinterpret_cast<__nv_bfloat16*>(Abuf + a_off(row, k2)) = __float2bfloat16_rn(0.f);
+            }
         }
         tc::fence_proxy_async_smem();
     }
     __syncthreads();
 
     // ---- layer 1 ----
-    if (issuer) {
-        if (!*abort_flag && !run_chunks(0, n1)) *abort_flag = 1;
-        tc::mma_commit(done);   // completes once every MMA issued so far is done
-    }
+    if (issuer) run_layer(0, nkb);
     bool ok = true;
-    if (warp < 4) {
-        ok = wait_or_abort(done, 0, abort_flag) && !*abort_flag;
+    if (warp < kEpiWarps) {
+        // a1 overwrites the input tile, which every layer-1 MMA reads: both
+        // halves wait for the whole layer (done[1] follows all of it)
+        ok = wait_or_abort(&done[1], 0, abort_flag) && !*abort_flag;
         __syncwarp();
         tc::tc_fence_after();
         if (ok) {
-            const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-            const int row = tid;
             unsigned char* rbase = Abuf + row * 128;
-            for (int cb = 0; cb < kHid / 16; ++cb) {
+            for (int cb = half * 8; cb < half * 8 + 8; ++cb) {
                 float v[16];
                 tc::tmem_ld16(lane_base + 16 * cb, v);
                 uint32_t w[8];
@@ -235,21 +263,18 @@ __global__ void __launch_bounds__(160, 1) mlp_infer_kernel(const __grid_constant
     }
     __syncthreads();
 
-    // ---- layer 2 ----
+    // ---- layer 2, then the FP32 output layer ----
     if (issuer) {
         tc::tc_fence_after();
-        if (!*abort_flag && !run_chunks(n1, nch)) *abort_flag = 1;
-        tc::mma_commit(done);
+        run_layer(n1, 4);
     }
-    if (warp < 4) {
-        ok = ok && wait_or_abort(done, 1, abort_flag) && !*abort_flag;
+    if (warp < kEpiWarps) {
+        ok = ok && wait_or_abort(&done[half], 1, abort_flag) && !*abort_flag;
         __syncwarp();
         tc::tc_fence_after();
-        const int64_t f = f0 + tid;
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
         if (ok) {
-            const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-            float o[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int cb = 0; cb < kHid / 16; ++cb) {
+            for (int cb = half * 8; cb < half * 8 + 8; ++cb) {
                 float v[16];
                 tc::tmem_ld16(lane_base + 16 * cb, v);
 #pragma unroll
@@ -260,31 +285,37 @@ __global__ void __launch_bounds__(160, 1) mlp_infer_kernel(const __grid_constant
                     for (int j = 0; j < 4; ++j) o[j] = fmaf(tab[kMlpTabW3 + j * kHid + c], h, o[j]);
                 }
             }
-            if (f < a.n) {
-                float p[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    p[j] = fmaf(o[j] + tab[kMlpTabB3 + j], tab[kMlpTabOutScale + j], tab[kMlpTabOutMean + j]);
-                p[1] = fminf(fmaxf(fabsf(p[1]), a.g_lo), a.g_hi);
-                if (!(fabsf(p[0]) < INFINITY && fabsf(p[1]) < INFINITY && fabsf(p[2]) < INFINITY &&
-                      fabsf(p[3]) < INFINITY)) {
-                    // no usable guess: a flat start the polish cannot converge
-                    // from, so the frame goes to the moment-guess fallback
-                    p[0] = a.x_mid;
-                    p[1] = a.g_lo;
-                    p[2] = 0.f;
-                    p[3] = 0.f;
-                }
-                float* q = a.p0 + f * 4;
-                q[0] = p[0];
-                q[1] = p[1];
-                q[2] = p[2];
-                q[3] = p[3];
-                if (a.flags) a.flags[f] = 0;
-            }
-        } else if (tid == 0) {
-            atomicExch(a.err, 2);
         }
+        if (half == 1) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) red[row * 4 + j] = o[j];
+        }
+        asm volatile("bar.sync 1, %0;\n" ::"n"(kEpiWarps * 32) : "memory");   // the epilogue warps only
+        const int64_t f = f0 + row;
+        if (half == 0 && ok && f < a.n) {
+            float p[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                p[j] = fmaf(o[j] + red[row * 4 + j] + tab[kMlpTabB3 + j], tab[kMlpTabOutScale + j],
+                            tab[kMlpTabOutMean + j]);
+            p[1] = fminf(fmaxf(fabsf(p[1]), a.g_lo), a.g_hi);
+            if (!(fabsf(p[0]) < INFINITY && fabsf(p[1]) < INFINITY && fabsf(p[2]) < INFINITY &&
+                  fabsf(p[3]) < INFINITY)) {
+                // no usable guess: a flat start the polish cannot converge
+                // from, so the frame goes to the moment-guess fallback
+                p[0] = a.x_mid;
+                p[1] = a.g_lo;
+                p[2] = 0.f;
+                p[3] = 0.f;
+            }
+            float* q = a.p0 + f * 4;
+            q[0] = p[0];
+            q[1] = p[1];
+            q[2] = p[2];
+            q[3] = p[3];
+            if (a.flags) a.flags[f] = 0;
+        }
+        if (!ok && tid == 0) atomicExch(a.err, 2);
     }
 
     // ---- teardown: drain loads still in flight after an abort, free TMEM ----
@@ -293,7 +324,7 @@ __global__ void __launch_bounds__(160, 1) mlp_infer_kernel(const __grid_constant
     }
     tc::tc_fence_before();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == kEpiWarps) {
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, kHid);
     }
@@ -317,7 +348,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
 
 int mlp_smem_bytes(int stages, int T)
 {
-    return 1024 + kABytes + stages * kChunkBytes + 4 * (kMlpTabIn + 2 * T) + 8 * (2 * kStagesMax + 1) + 16;
+    return 1024 + kABytes + stages * kChunkBytes + 4 * (kMlpTabIn + 2 * T) + 4 * 4 * kMM + 8 * (2 * kStagesMax + 2) +
+           16;
 }
 
 // Parses a cg_mlp_save blob, packs the BF16 weight matrix, the FP32 tables and
@@ -442,7 +474,7 @@ cudaError_t launch_mlp(const cg_plan_s* p, const float* y, const float* amps, in
     m.flags = flags;
     const unsigned grid = static_cast<unsigned>((n + kMM - 1) / kMM);
     void* args[] = {const_cast<CUtensorMap*>(&p->mlp_map), &m};
-    return cudaLaunchKernel(reinterpret_cast<void*>(&mlp_infer_kernel), dim3(grid), dim3(160), args, p->mlp_smem, s);
+    return cudaLaunchKernel(reinterpret_cast<void*>(&mlp_infer_kernel), dim3(grid), dim3(kMlpThreads), args, p->mlp_smem, s);
 }
 
 }  // namespace cg
