@@ -327,6 +327,10 @@ def run_ours(args):
         result.update(cpu_baseline_leg(frames, params, status, iters, plan, ref, g, args))
     if not args.quick:
         result["e2e"] = run_e2e(plan, frames, n, T, dev, args, ws)
+    if not args.quick and args.serve_seconds > 0 and rank == 0:
+        del frames, amps, params, rss, iters, status
+        torch.cuda.empty_cache()
+        result["serving"] = run_serving(args, dev)
     if rank == 0:
         print(json.dumps(result), flush=True)
     plan.close()
@@ -392,6 +396,108 @@ def run_e2e(plan, frames_dev, n, T, dev, args, ws):
             "input_gbs": n * ws * N * 2 / dt / 1e9}
 
 
+SERVE_STREAMS = [   # (geometry attribute, generator keywords): the three instruments of the serving workload
+    ("PAPER_RATE", dict(snr_db=30.0, center_amp_hz=20e6)),
+    ("WIDE", dict(snr_db=30.0, center_amp_hz=20e6)),
+    ("SERVE_4096", dict(snr_db=30.0, center_amp_hz=20e6)),
+]
+
+
+def run_serving(args, dev) -> dict:
+    """Streaming leg: three instrument streams (1100 @ 1.1 GS/s, 2500 @ 2.5 GS/s,
+    4096 @ 2.0 GS/s) pushed in real time from pinned pools of pre-generated
+    frames (replayed with fresh sequence numbers) into one server; each
+    result's latency is its poll-ready time minus the acquisition time of the
+    first frame of its push.  Reports sustained rates and p50 / p99 latency."""
+    import threading
+    import torch
+    import paper_2307_12988_gb300 as cg
+    import synth
+    server = cg.Server(args.serve_budget)
+    streams, pools, plans = [], [], []
+    for i, (gname, kw) in enumerate(SERVE_STREAMS):
+        g = getattr(synth, gname)
+        st = synth.make_stream(g, synth.BASE_SEED + 800 + i)
+        pool = synth.frames(st, args.serve_pool, device=dev, **kw)["frames"].cpu().numpy()
+        rf = synth.frames(st, 4096, cavity=False, noise_stream=1, device=dev, snr_db=30.0)["frames"]
+        p0 = cg.Plan(g.sample_rate, g.frame_len, g.tooth_freqs, g.tooth_x)
+        ref = p0.reference_accumulate(rf)
+        p0.close()
+        plan = cg.Plan(g.sample_rate, g.frame_len, g.tooth_freqs, g.tooth_x, ref)
+        period = g.frame_len / g.sample_rate
+        chunk = max(1, int(round(args.serve_push_s / period)))
+        ring = 2 * g.frame_len * max(8 * args.serve_batch, int(args.serve_ring_s / period))
+        s = cg.Stream(server, plan, ring_bytes=ring, batch_frames=args.serve_batch,
+                      max_delay_s=args.serve_delay, avg_window=10_000)
+        streams.append((g, s, period, chunk))
+        pools.append(pool)
+        plans.append(plan)
+    stop = threading.Event()
+    counts = [dict(pushed=0, overflow=0, polled=0) for _ in streams]
+    t0 = cg.cg_clock() + 0.05
+
+    def producer(i):
+        g, s, period, chunk = streams[i]
+        pool = pools[i]
+        k, seq = 0, 0
+        while not stop.is_set():
+            t_acq = t0 + seq * period                      # acquisition time of the chunk's first frame
+            t_ready = t_acq + chunk * period               # the chunk is complete
+            while cg.cg_clock() < t_ready:
+                time.sleep(max(0.0, min(2e-4, t_ready - cg.cg_clock())))
+            if cg.cg_clock() - t0 > args.serve_seconds:
+                break
+            if k + chunk > pool.shape[0]:
+                k = 0
+            st = s.push(pool[k:k + chunk], seq, t_acq)
+            if st == 0:
+                counts[i]["pushed"] += chunk
+            else:
+                counts[i]["overflow"] += chunk
+            k += chunk
+            seq += chunk
+
+    def consumer(i):
+        _, s, _, _ = streams[i]
+        while not stop.is_set() or s.stats()["frames_polled"] < s.stats()["frames_pushed"]:
+            r, _, _ = s.poll(cap=65536, timeout_s=0.05)
+            counts[i]["polled"] += len(r)
+            if stop.is_set() and len(r) == 0 and s.flush(5.0) != 0:
+                break
+
+    threads = [threading.Thread(target=producer, args=(i,)) for i in range(len(streams))]
+    threads += [threading.Thread(target=consumer, args=(i,)) for i in range(len(streams))]
+    for t in threads:
+        t.start()
+    for t in threads[:len(streams)]:
+        t.join()
+    stop.set()
+    for t in threads[len(streams):]:
+        t.join()
+    out = {"seconds": args.serve_seconds, "batch_frames": args.serve_batch, "max_delay_s": args.serve_delay,
+           "push_s": args.serve_push_s, "device_budget_bytes": args.serve_budget, "streams": []}
+    tot_frames, tot_bytes = 0, 0.0
+    for (g, s, period, chunk), c in zip(streams, counts):
+        st = s.stats()
+        out["streams"].append({
+            "frame_len": g.frame_len, "teeth": g.n_teeth, "sample_rate_hz": g.sample_rate,
+            "offered_gbs": 2 * g.frame_len / period / 1e9, "input_gbs": st["input_bytes_per_s"] / 1e9,
+            "frames_done": st["frames_done"], "frames_dropped": st["frames_dropped"],
+            "latency_p50_ms": st["latency_p50_s"] * 1e3, "latency_p99_ms": st["latency_p99_s"] * 1e3,
+            "latency_max_ms": st["latency_max_s"] * 1e3, "batches": st["batches"],
+            "windows_completed": st["window_index"] + 1})
+        tot_frames += st["frames_done"]
+        tot_bytes += st["input_bytes_per_s"]
+        s.close()
+    for p in plans:
+        p.close()
+    server.close()
+    out["spectra_per_s"] = tot_frames / args.serve_seconds
+    out["input_gbs"] = tot_bytes / 1e9
+    out["latency_p99_ms_max"] = max(x["latency_p99_ms"] for x in out["streams"])
+    return out
+
+
 def run_reference(args):
     """The oracle as it stands on the host cores, on the same metric."""
     ws, rank, local = _dist()
@@ -454,9 +560,22 @@ def main():
     ap.add_argument("--e2e-chunk", type=int, default=65536)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-impl-frames", type=int, default=20000)
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="streaming leg duration (the serving workload runs 60 s per stream)")
+    ap.add_argument("--serve-only", action="store_true", help="run only the streaming leg")
+    ap.add_argument("--serve-batch", type=int, default=4096)
+    ap.add_argument("--serve-delay", type=float, default=5e-4)
+    ap.add_argument("--serve-push-s", type=float, default=2.5e-4, help="acquisition time per push")
+    ap.add_argument("--serve-ring-s", type=float, default=0.25, help="ring length in seconds of data")
+    ap.add_argument("--serve-pool", type=int, default=32768, help="pre-generated frames replayed per stream")
+    ap.add_argument("--serve-budget", type=int, default=4 << 30)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"serving": run_serving(args, torch.device("cuda", 0))}), flush=True)
     else:
         run_ours(args)
 

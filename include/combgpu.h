@@ -353,6 +353,139 @@ cg_status cg_mlp_load(cg_plan_t plan, const void* blob_host, size_t bytes);
 cg_status cg_mlp_infer(cg_plan_t plan, const float* y_dev, int64_t n, float* p0_dev,
                        void* cuda_stream);
 
+/*
+ * ---- Streaming ---------------------------------------------------------------
+ * The paper's acquisition loop ("Data Capture and Processing"): the digitiser
+ * fills a ring buffer on the host while the GPU processes earlier batches;
+ * batches finish out of order and are sorted back into time order; the
+ * production rate must not exceed the consumption rate, or the ring
+ * overflows.  Here a server (one scheduler thread per GPU) serves several
+ * instrument streams, each with its own plan (geometry), pinned host ring and
+ * result queue:
+ *   - continuous batching: whenever a stream has a batch of frames waiting
+ *     (or its oldest frame has waited max_delay) and one of its device batch
+ *     buffers is free, the batch is copied to the device and processed on its
+ *     own CUDA stream, overlapping other batches and other streams;
+ *   - admission by device memory: a stream's batch buffers (frames, outputs)
+ *     are granted from the server's budget; a stream that does not fit waits,
+ *     with its ring still accepting frames, until memory is returned;
+ *   - running averages on the device: FP64 means of y_k and of the fit
+ *     parameters over consecutive windows of avg_window frames;
+ *   - results are handed out in push order with their latency (result time
+ *     minus arrival time), whose p50 / p99 the stream reports.
+ * A frame's ring slot is reused only after its result has been polled, so a
+ * consumer that does not keep up makes cg_stream_push overflow.
+ * No call waits without a bound: every wait takes a timeout and returns
+ * CG_ERR_TIMEOUT when it runs out.
+ */
+typedef struct cg_server_s* cg_server_t;
+typedef struct cg_stream_s* cg_stream_t;
+
+typedef struct cg_result {
+    uint64_t seq;         /* sequence number: first_seq of its push + index */
+    double t_arrival;     /* arrival time (cg_clock seconds) given at push */
+    double t_done;        /* time its result became available to cg_stream_poll */
+    float params[4];      /* (c, g, A, B) as cg_process */
+    float rss;
+    int16_t iters;
+    int16_t status;
+} cg_result;
+
+typedef struct cg_stream_stats_t {
+    int64_t frames_pushed;    /* accepted into the ring */
+    int64_t frames_dropped;   /* rejected by cg_stream_push (overflow) */
+    int64_t frames_done;      /* results produced */
+    int64_t frames_polled;    /* results taken by cg_stream_poll */
+    int64_t batches;          /* batches processed */
+    double latency_p50_s;     /* over every result so far (1 % bins) */
+    double latency_p99_s;
+    double latency_max_s;
+    double input_bytes_per_s; /* frame bytes processed / (last result - first push) */
+    int admitted;             /* 1 once device memory was granted */
+    int64_t window_index;     /* last completed running-average window, -1 if none */
+    int64_t window_frames;    /* frames averaged in it (converged fits only) */
+} cg_stream_stats_t;
+
+/* Seconds on the library's monotonic clock (the time base of t_arrival). */
+double cg_clock(void);
+
+/*
+ * cg_server_create -- scheduler for the current device.  device_budget_bytes
+ * bounds the batch buffers of all its streams together (> 0).
+ */
+cg_status cg_server_create(cg_server_t* server, size_t device_budget_bytes);
+
+/* Stop the scheduler (destroying any stream still open) and free everything. */
+cg_status cg_server_destroy(cg_server_t server);
+
+/*
+ * Host-side fault injection for tests (no GPU fault is ever provoked):
+ *   CG_INJECT_THROTTLE_S: the scheduler sleeps value seconds before each batch
+ *                         launch (a consumer slower than the producer);
+ *   CG_INJECT_HOLD:       value != 0 holds back every completed batch (a stalled
+ *                         pipeline), 0 releases them;
+ *   CG_INJECT_FAIL_LAUNCH: the next value batch launches fail as if the launch
+ *                         call had returned an error; the stream enters its
+ *                         error state (CG_ERR_CUDA).
+ */
+enum { CG_INJECT_THROTTLE_S = 1, CG_INJECT_HOLD = 2, CG_INJECT_FAIL_LAUNCH = 3 };
+cg_status cg_server_inject(cg_server_t server, int what, double value);
+
+/*
+ * cg_stream_create -- an instrument stream on a server.
+ *   plan          geometry and options (not owned; must outlive the stream and
+ *                 is used only by the scheduler thread while the stream lives)
+ *   ring_bytes    pinned host ring for the stream's frames (>= 2 batches)
+ *   batch_frames  frames per batch (>= 1)
+ *   max_delay_s   a partial batch is launched once its oldest frame has waited
+ *                 this long (>= 0)
+ *   avg_window    frames per running-average window (>= 1)
+ * Admission needs 2 batch buffers within the server's remaining budget; up to
+ * 4 are used when the budget allows.  Errors: CG_ERR_ARG, CG_ERR_NOMEM (pinned
+ * ring), CG_ERR_UNSUPPORTED (2 batch buffers exceed the whole budget).
+ */
+cg_status cg_stream_create(cg_stream_t* stream, cg_server_t server, cg_plan_t plan,
+                           size_t ring_bytes, int batch_frames, double max_delay_s,
+                           int64_t avg_window);
+
+/*
+ * cg_stream_push -- copy n frames (host int16 [n][N]) into the ring.  If the
+ * ring lacks room for all n, none is taken: CG_ERR_OVERFLOW, and the n frames
+ * count as dropped.  t_arrival < 0 stamps cg_clock().  Thread-safe against
+ * cg_stream_poll; one pushing thread per stream.
+ */
+cg_status cg_stream_push(cg_stream_t stream, const int16_t* frames_host, int64_t n,
+                         uint64_t first_seq, double t_arrival);
+
+/*
+ * cg_stream_poll -- take up to cap results in push order: recs (host
+ * cg_result [cap]) and, if amps_host is not NULL, their tooth magnitudes
+ * (host float [cap][T]).  Waits up to timeout_s for the first result; *n_out
+ * = 0 and CG_ERR_TIMEOUT if none came.  Returns the stream's error status if it
+ * entered its error state.
+ */
+cg_status cg_stream_poll(cg_stream_t stream, cg_result* recs, float* amps_host, int64_t cap,
+                         int64_t* n_out, double timeout_s);
+
+/* Launch the frames still waiting and wait (up to timeout_s) until every
+ * pushed frame has a result ready to poll. */
+cg_status cg_stream_flush(cg_stream_t stream, double timeout_s);
+
+cg_status cg_stream_stats(cg_stream_t stream, cg_stream_stats_t* stats);
+
+/*
+ * cg_stream_window -- means of the last completed running-average window:
+ * mean_y_host double [T] (y = |X| / reference) and mean_params_host double [4],
+ * over the window's frames whose fit converged.  *index = -1 if no window has
+ * completed yet.  Any output pointer may be NULL.
+ */
+cg_status cg_stream_window(cg_stream_t stream, int64_t* index, int64_t* count,
+                           double* mean_y_host, double* mean_params_host);
+
+/* Wait (bounded) for the stream's batches, free its ring and buffers and
+ * return its device memory to the server. */
+cg_status cg_stream_destroy(cg_stream_t stream);
+
 /* Text of a status code (static storage). */
 const char* cg_status_string(cg_status status);
 

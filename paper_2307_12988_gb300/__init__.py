@@ -18,12 +18,16 @@ from ._binding import (cg_mlp_adam, cg_mlp_backward, cg_mlp_create, cg_mlp_destr
                        cg_mlp_get_params, cg_mlp_infer, cg_mlp_load, cg_mlp_param_count, cg_mlp_save,
                        cg_mlp_set_norm, cg_mlp_set_params, cg_mlp_train_epoch, cg_timing_collect,
                        cg_timing_enable)
+from ._binding import (RESULT_DTYPE, INJECT_FAIL_LAUNCH, INJECT_HOLD, INJECT_THROTTLE_S, cg_clock,
+                       cg_server_create, cg_server_destroy, cg_server_inject, cg_stream_create,
+                       cg_stream_destroy, cg_stream_flush, cg_stream_poll, cg_stream_push,
+                       cg_stream_stats, cg_stream_window)
 from ._binding import (FFT_AUTO, FFT_COSET, FFT_FULL, FIT_CONVERGED, FIT_FALLBACK, FIT_INIT_FLAT,
                        FIT_MAX_ITER, FIT_NONFINITE, FIT_SINGULAR, INIT_MLP, INIT_MOMENT,
                        READOUT_FFT, READOUT_GEMM_SPLIT, PATH_AUTO, PATH_FUSED, PATH_SPLIT,
                        PATH_PIPELINE)
 
-__all__ = ["Plan", "Mlp", "CgError", "load", "cg_plan", "cg_plan_destroy", "cg_plan_describe",
+__all__ = ["Plan", "Mlp", "Server", "Stream", "CgError", "load", "cg_plan", "cg_plan_destroy", "cg_plan_describe",
            "cg_process", "cg_readout", "cg_fit", "cg_reference_accumulate",
            "cg_set_reference", "cg_opts_default", "cg_status_string", "cg_version"]
 
@@ -177,3 +181,67 @@ class Mlp:
 
     def save(self) -> bytes:
         return cg_mlp_save(self.handle)
+
+
+class Server:
+    """Streaming scheduler on the current device (``cg_server_*``)."""
+
+    def __init__(self, device_budget_bytes: int):
+        self.handle = cg_server_create(device_budget_bytes)
+
+    def inject(self, what: int, value: float):
+        cg_server_inject(self.handle, what, value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cg_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Stream:
+    """One instrument stream on a Server (``cg_stream_*``); the plan must
+    outlive it.  Frames are pushed from host numpy arrays."""
+
+    def __init__(self, server: Server, plan: Plan, ring_bytes: int, batch_frames: int,
+                 max_delay_s: float = 1e-3, avg_window: int = 10_000):
+        self.plan = plan
+        self.T = plan.T
+        self.handle = cg_stream_create(server.handle, plan.handle, ring_bytes, batch_frames,
+                                       max_delay_s, avg_window)
+
+    def push(self, frames: np.ndarray, first_seq: int, t_arrival: float = -1.0) -> int:
+        f = np.ascontiguousarray(frames, dtype=np.int16)
+        return cg_stream_push(self.handle, f, f.shape[0], first_seq, t_arrival)
+
+    def poll(self, cap: int = 65536, timeout_s: float = 0.0, want_amps: bool = False):
+        """(results array of RESULT_DTYPE, amps [k, T] or None, status)."""
+        recs = np.empty(cap, dtype=RESULT_DTYPE)
+        amps = np.empty((cap, self.T), dtype=np.float32) if want_amps else None
+        k, st = cg_stream_poll(self.handle, recs, amps, timeout_s)
+        return recs[:k], (amps[:k] if want_amps else None), st
+
+    def flush(self, timeout_s: float = 30.0) -> int:
+        return cg_stream_flush(self.handle, timeout_s)
+
+    def stats(self) -> dict:
+        return cg_stream_stats(self.handle)
+
+    def window(self) -> dict:
+        return cg_stream_window(self.handle, self.T)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cg_stream_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -60,6 +60,28 @@ class cg_plan_info(ctypes.Structure):
                 ("n_collisions", ctypes.c_int), ("path", ctypes.c_int)]
 
 
+class cg_result(ctypes.Structure):
+    _fields_ = [("seq", ctypes.c_uint64), ("t_arrival", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("params", ctypes.c_float * 4), ("rss", ctypes.c_float), ("iters", ctypes.c_int16),
+                ("status", ctypes.c_int16)]
+
+
+RESULT_DTYPE = np.dtype([("seq", np.uint64), ("t_arrival", np.float64), ("t_done", np.float64),
+                         ("params", np.float32, 4), ("rss", np.float32), ("iters", np.int16),
+                         ("status", np.int16)], align=True)
+
+
+class cg_stream_stats_t(ctypes.Structure):
+    _fields_ = [("frames_pushed", ctypes.c_int64), ("frames_dropped", ctypes.c_int64),
+                ("frames_done", ctypes.c_int64), ("frames_polled", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("latency_p50_s", ctypes.c_double),
+                ("latency_p99_s", ctypes.c_double), ("latency_max_s", ctypes.c_double),
+                ("input_bytes_per_s", ctypes.c_double), ("admitted", ctypes.c_int),
+                ("window_index", ctypes.c_int64), ("window_frames", ctypes.c_int64)]
+
+
+INJECT_THROTTLE_S, INJECT_HOLD, INJECT_FAIL_LAUNCH = 1, 2, 3
+
 _P = ctypes.c_void_p
 _SIGS = {
     "cg_opts_default": (None, [ctypes.POINTER(cg_opts)]),
@@ -92,6 +114,20 @@ _SIGS = {
     "cg_mlp_save": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "cg_mlp_load": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "cg_mlp_infer": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    "cg_clock": (ctypes.c_double, []),
+    "cg_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_size_t]),
+    "cg_server_destroy": (ctypes.c_int, [_P]),
+    "cg_server_inject": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
+    "cg_stream_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P, ctypes.c_size_t, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_int64]),
+    "cg_stream_push": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double]),
+    "cg_stream_poll": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.c_double]),
+    "cg_stream_flush": (ctypes.c_int, [_P, ctypes.c_double]),
+    "cg_stream_stats": (ctypes.c_int, [_P, ctypes.POINTER(cg_stream_stats_t)]),
+    "cg_stream_window": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                        _P, _P]),
+    "cg_stream_destroy": (ctypes.c_int, [_P]),
     "cg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cg_last_error": (ctypes.c_char_p, []),
     "cg_version": (ctypes.c_int, []),
@@ -324,6 +360,79 @@ def cg_mlp_load(plan: int, blob: bytes) -> None:
 
 def cg_mlp_infer(plan: int, y, n: int, p0, stream=None) -> None:
     _check(load().cg_mlp_infer(plan, _ptr(y), int(n), _ptr(p0), _stream(stream)), "cg_mlp_infer")
+
+
+def cg_clock() -> float:
+    return float(load().cg_clock())
+
+
+def cg_server_create(device_budget_bytes: int) -> int:
+    h = _P()
+    _check(load().cg_server_create(ctypes.byref(h), int(device_budget_bytes)), "cg_server_create")
+    return h.value
+
+
+def cg_server_destroy(server: int) -> None:
+    if server:
+        _check(load().cg_server_destroy(server), "cg_server_destroy")
+
+
+def cg_server_inject(server: int, what: int, value: float) -> None:
+    _check(load().cg_server_inject(server, int(what), float(value)), "cg_server_inject")
+
+
+def cg_stream_create(server: int, plan: int, ring_bytes: int, batch_frames: int, max_delay_s: float,
+                     avg_window: int) -> int:
+    h = _P()
+    _check(load().cg_stream_create(ctypes.byref(h), server, plan, int(ring_bytes), int(batch_frames),
+                                   float(max_delay_s), int(avg_window)), "cg_stream_create")
+    return h.value
+
+
+def cg_stream_push(stream: int, frames_host, n: int, first_seq: int, t_arrival: float = -1.0) -> int:
+    """Returns the status code (CG_OK or CG_ERR_OVERFLOW) instead of raising on overflow."""
+    st = load().cg_stream_push(stream, _ptr(frames_host), int(n), int(first_seq), float(t_arrival))
+    if st not in (CG_OK, 5):
+        _check(st, "cg_stream_push")
+    return st
+
+
+def cg_stream_poll(stream: int, recs: np.ndarray, amps_host=None, timeout_s: float = 0.0) -> tuple[int, int]:
+    """Fill recs (RESULT_DTYPE array); returns (count, status) with status CG_OK or
+    CG_ERR_TIMEOUT (other errors raise)."""
+    n = ctypes.c_int64(0)
+    st = load().cg_stream_poll(stream, _ptr(recs), _ptr(amps_host), int(recs.shape[0]), ctypes.byref(n),
+                               float(timeout_s))
+    if st not in (CG_OK, 6):
+        _check(st, "cg_stream_poll")
+    return int(n.value), st
+
+
+def cg_stream_flush(stream: int, timeout_s: float) -> int:
+    st = load().cg_stream_flush(stream, float(timeout_s))
+    if st not in (CG_OK, 6):
+        _check(st, "cg_stream_flush")
+    return st
+
+
+def cg_stream_stats(stream: int) -> dict:
+    o = cg_stream_stats_t()
+    _check(load().cg_stream_stats(stream, ctypes.byref(o)), "cg_stream_stats")
+    return {name: getattr(o, name) for name, _ in cg_stream_stats_t._fields_}
+
+
+def cg_stream_window(stream: int, n_teeth: int) -> dict:
+    idx, cnt = ctypes.c_int64(0), ctypes.c_int64(0)
+    y = np.full(n_teeth, np.nan)
+    p = np.full(4, np.nan)
+    _check(load().cg_stream_window(stream, ctypes.byref(idx), ctypes.byref(cnt), _ptr(y), _ptr(p)),
+           "cg_stream_window")
+    return {"index": idx.value, "count": cnt.value, "mean_y": y, "mean_params": p}
+
+
+def cg_stream_destroy(stream: int) -> None:
+    if stream:
+        _check(load().cg_stream_destroy(stream), "cg_stream_destroy")
 
 
 def cg_status_string(status: int) -> str:

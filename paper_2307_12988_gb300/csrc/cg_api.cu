@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -201,7 +202,7 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
     a.inv_ref = p->d.inv_ref;
     a.u = p->d.u;
     void* fr = cg::fast_readout_ptr(Q);
-    if ((e = cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, a.sm_total)) != cudaSuccess) return e;
+    if ((e = cg::raise_smem_limit(fr, a.sm_total)) != cudaSuccess) return e;
     int occ = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fr, 128, a.sm_total)) != cudaSuccess) return e;
     if (occ < 1) return cudaSuccess;
@@ -247,13 +248,13 @@ cudaError_t setup_fit_kernels(cg_plan_s* p)
     int occ = 0;
     void* ff = cg::fit2_ptr(G, ppl, exact);
     const size_t fsm = cg::fit2_smem(G, T);
-    if ((e = cudaFuncSetAttribute(ff, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(fsm))) != cudaSuccess) return e;
+    if ((e = cg::raise_smem_limit(ff, static_cast<int>(fsm))) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ff, cg::fit2_threads(G), fsm)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&p->d.fit_counter, sizeof(unsigned long long))) != cudaSuccess) return e;
     if (occ < 1) return cudaSuccess;
     p->grid_fit2 = p->num_sms * occ;
     void* fi = cg::init_ptr(npad);
-    if ((e = cudaFuncSetAttribute(fi, cudaFuncAttributeMaxDynamicSharedMemorySize, p->init_smem)) != cudaSuccess) return e;
+    if ((e = cg::raise_smem_limit(fi, p->init_smem)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fi, 128, p->init_smem)) != cudaSuccess) return e;
     if (occ < 1) return cudaSuccess;
     p->grid_init = p->num_sms * occ;
@@ -281,6 +282,17 @@ std::vector<float> inv_ref_of(const std::vector<double>& ref)
 }  // namespace
 
 void cg::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+cudaError_t cg::raise_smem_limit(const void* fn, int bytes)
+{
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    cudaFuncAttributes at;
+    cudaError_t e = cudaFuncGetAttributes(&at, fn);
+    if (e != cudaSuccess) return e;
+    if (at.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
 
 namespace {
 

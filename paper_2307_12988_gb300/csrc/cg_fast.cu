@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
             for (int i = threadIdx.x; i < nf * T; i += blockDim.x) {
                 const float av = amp_s[i];
                 if (a.amps) a.amps[f0 * T + i] = av;
-                if (a.y) a.y[f0 * T + i] = av * iref[k];
+                if (a.y) a.y[f0 * T + i] = __fmul_rn(av, iref[k]);
                 k += blockDim.x;
                 while (k >= T) k -= T;
             }
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
             for (int f = 0; f < nf; ++f) {
                 const int64_t fr = a.list[f0 + f];
                 const float* src = (a.y ? a.y : a.amps) + fr * T;
-                for (int k = lane; k < T; k += 32) rows[f * TS + k] = a.y ? src[k] : src[k] * iref[k];
+                for (int k = lane; k < T; k += 32) rows[f * TS + k] = a.y ? src[k] : __fmul_rn(src[k], iref[k]);
             }
         } else {
             // the 32 rows are contiguous in global memory: one flat coalesced
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int e = e0 + q * 32 + lane;
-                    if (e < total) rows[f * TS + k] = a.y ? v[q] : v[q] * iref[k];
+                    if (e < total) rows[f * TS + k] = a.y ? v[q] : __fmul_rn(v[q], iref[k]);
                     k += 32;
                     while (k >= T) {
                         k -= T;
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
 #pragma unroll
                 for (int j = 0; j < PPL; ++j) {
                     const int k = gl + G * j;
-                    yv[j] = (k < T) ? src[k] * iref[k] : 0.f;
+                    yv[j] = (k < T) ? __fmul_rn(src[k], iref[k]) : 0.f;
                 }
             }
             const float* q = a.p0 + fr * 4;

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(128) fit1_kernel(Fit2Args a)
         if (scale_rows) {
             const float* ir = a.inv_ref;
 #pragma unroll 4
-            for (int k = 0; k < T; ++k) accum_point(us[k], my[k] * __ldg(ir + k), c, g2, A, B, S);
+            for (int k = 0; k < T; ++k) accum_point(us[k], __fmul_rn(my[k], __ldg(ir + k)), c, g2, A, B, S);
         } else {
 #pragma unroll 4
             for (int k = 0; k < T; ++k) accum_point(us[k], my[k], c, g2, A, B, S);

@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(192, 1) dft_gemm_kernel(const __grid_constant_
                         if (tooth < a.T) {
                             const float amp = sqrtf(fmaf(v[2 * i], v[2 * i], v[2 * i + 1] * v[2 * i + 1]));
                             if (a.amps) a.amps[f * a.T + tooth] = amp;
-                            if (a.y) a.y[f * a.T + tooth] = amp * a.inv_ref[tooth];
+                            if (a.y) a.y[f * a.T + tooth] = __fmul_rn(amp, a.inv_ref[tooth]);
                         }
                     }
                 }
@@ -393,7 +393,7 @@ cudaError_t setup_gemm(cg_plan_s* p)
     p->gemm_smem = 1024 + stages * stage_bytes + 8 * (3 * kPipeMax + 1) + 16;
     p->gemm_ntiles = ntiles;
     void* fn = split ? reinterpret_cast<void*>(&dft_gemm_kernel<true>) : reinterpret_cast<void*>(&dft_gemm_kernel<false>);
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->gemm_smem);
+    return raise_smem_limit(fn, p->gemm_smem);
 }
 
 cudaError_t launch_gemm_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps, float* y,

@@ -289,4 +289,9 @@ cudaError_t launch_gemm_readout(const cg_plan_s* p, const int16_t* frames, int64
 // sets the thread-local text returned by cg_last_error()
 void set_last_error(const char* msg);
 
+// Raises (never lowers) a kernel's dynamic shared-memory limit.  The limit
+// belongs to the function on the device, so every plan shares it: one plan
+// must not shrink what another plan's launches need.
+cudaError_t raise_smem_limit(const void* fn, int bytes);
+
 }  // namespace cg

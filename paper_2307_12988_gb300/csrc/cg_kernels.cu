@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kThreads) readout_kernel(ReadoutArgs a, FitArg
             if (MODE == 2) {
                 atomicAdd(&acc[k], static_cast<double>(amp));
             } else {
-                const float yv = amp * iref[k];
+                const float yv = __fmul_rn(amp, iref[k]);
                 if (a.amps) a.amps[o] = amp;
                 if (a.y) a.y[o] = yv;
                 if (MODE == 1) ys[f * a.ystride + k] = yv;
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kThreads) fit_kernel(FitArgs fa, int ystride)
         for (int i = threadIdx.x; i < nf * T; i += blockDim.x) {
             const int f = i / T;
             const int k = i - f * T;
-            ys[f * ystride + k] = fa.y ? fa.y[f0 * T + i] : fa.amps_in[f0 * T + i] * fa.inv_ref[k];
+            ys[f * ystride + k] = fa.y ? fa.y[f0 * T + i] : __fmul_rn(fa.amps_in[f0 * T + i], fa.inv_ref[k]);
         }
         __syncthreads();
         const bool valid = group < nf;
@@ -312,7 +312,7 @@ cudaError_t configure_kernels(cg_plan_s* p)
     for (int mode = 0; mode < 3; ++mode) {
         void* fn = readout_ptr(mode, G);
         if (!fn) return cudaErrorInvalidValue;
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->ra.sm_total);
+        e = raise_smem_limit(fn, p->ra.sm_total);
         if (e != cudaSuccess) return e;
     }
     int occ = 0;
@@ -324,7 +324,7 @@ cudaError_t configure_kernels(cg_plan_s* p)
     p->grid_fused = p->num_sms * (occ > 0 ? occ : 1);
     const int ys = fit_ystride(p->T, G);
     const int fit_smem = static_cast<int>(sizeof(float)) * (((p->T + 3) & ~3) + (kThreads / G) * ys);
-    e = cudaFuncSetAttribute(fit_ptr(G), cudaFuncAttributeMaxDynamicSharedMemorySize, fit_smem);
+    e = raise_smem_limit(fit_ptr(G), fit_smem);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fit_ptr(G), kThreads, fit_smem);
     if (e != cudaSuccess) return e;

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kMlpThreads, 2) mlp_infer_kernel(const __grid_
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 if (e0 + q * kE + tid < total) {
-                    float x = a.y ? v[q] : v[q] * __ldg(a.inv_ref + k);
+                    float x = a.y ? v[q] : __fmul_rn(v[q], __ldg(a.inv_ref + k));
                     x = (x - in_mean[k]) * in_scale[k];
                     *reinterpret_cast<__nv_bfloat16*>(Abuf + a_off(r, k)) = __float2bfloat16_rn(x);
                 }
@@ -456,8 +456,7 @@ cudaError_t setup_mlp(cg_plan_s* p, const unsigned char* blob, size_t bytes, con
     m.stages = 2;
     m.err = p->d.err;
     p->mlp_smem = mlp_smem_bytes(m.stages, p->T);
-    if ((e = cudaFuncSetAttribute(reinterpret_cast<void*>(&mlp_infer_kernel),
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, p->mlp_smem)) != cudaSuccess)
+    if ((e = raise_smem_limit(reinterpret_cast<void*>(&mlp_infer_kernel), p->mlp_smem)) != cudaSuccess)
         return e;
     p->mlp_ok = true;
     return cudaSuccess;

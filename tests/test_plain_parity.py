@@ -177,3 +177,17 @@ def test_results_independent_of_batching(dev):
             a = full[k][37:38].cpu().numpy()
             b = part[k].cpu().numpy()
             np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("name", ["paper_rate", "wide", "serve4096"])
+def test_results_independent_of_requesting_y(dev, name):
+    """Asking for y_dev or not changes nothing: without it the fit forms
+    y = amps / reference itself, with the same rounding as the readout."""
+    w = W.workload(name)
+    fr = torch.from_numpy(w["frames"]).to(dev)
+    with _plan(w) as p:
+        with_y = p.process(fr, want_y=True)
+        no_y = p.process(fr, want_y=False)
+        torch.cuda.synchronize()
+        for k in ("amps", "params", "rss", "iters", "status"):
+            np.testing.assert_array_equal(with_y[k].cpu().numpy(), no_y[k].cpu().numpy(), err_msg=k)
