@@ -145,6 +145,11 @@ def build_workload(args, n_frames, n_ref, device, seed_offset=0):
 
 MLP_BLOB = os.path.join(ROOT, "paper_2307_12988_gb300", "data", "mlp_wide_t221.cgmlp")
 
+# DRAM bytes per frame measured by ncu on the paper-rate workload (kernel
+# names as in the per-kernel timing); the capture is summarised with its
+# command in profiles/paper_rate_traffic.md
+NCU_TRAFFIC_PER_FRAME = {("paper_rate", "fft", "moment"): {"readout": 2518.8, "init": 396.3, "fit": 414.6}}
+
 # FP32 operations of one LM point evaluation (model, residual, Jacobian and
 # the 14 running sums of J^T J, J^T r and chi^2): 11 + 10 FMA x 2 + 4 adds
 LM_FLOP_PER_POINT = 35
@@ -177,6 +182,8 @@ def kernel_rooflines(stage_ms, stage_launches, n, g, T, args, mean_iters, hbm, b
             r.update(bound="alu", achieved=f / per / 1e12, peak=alu_peak, unit="TFLOP/s")
         if "achieved" in r:
             r["frac"] = r["achieved"] / r["peak"]
+        tr = NCU_TRAFFIC_PER_FRAME.get((args.workload, args.readout, args.init), {}).get(st)
+        r["traffic"] = tr * frames if tr is not None else None
         out[st] = r
     return out
 
@@ -314,7 +321,7 @@ def run_ours(args):
         "input_gbs": total_frames * 2 * g.frame_len / (ms_step / 1e3) / 1e9,
         "roofline": {"kernel": dominant, "bound": dom.get("bound"), "achieved": dom.get("achieved"),
                      "peak": dom.get("peak"), "unit": dom.get("unit"), "frac": dom.get("frac"),
-                     "traffic": None, "peak_kind": peak_kind},
+                     "traffic": dom.get("traffic"), "peak_kind": peak_kind},
         "step_hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "algorithmic_bytes_per_frame": bytes_per_frame},
         "kernels": kern,
