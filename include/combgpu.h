@@ -65,13 +65,14 @@ enum { CG_FFT_AUTO = 0, CG_FFT_FULL = 1, CG_FFT_COSET = 2 };
 enum { CG_INIT_MOMENT = 0, CG_INIT_MLP = 1 };
 /* Kernel arrangement of cg_process. */
 enum {
-    CG_PATH_AUTO = 0,      /* PIPELINE when the geometry admits it, else FUSED */
+    CG_PATH_AUTO = 0,      /* PIPELINE when the fit kernels cover n_teeth, else FUSED */
     CG_PATH_FUSED = 1,     /* one kernel: readout and fit per thread block */
     CG_PATH_SPLIT = 2,     /* a readout kernel, then a fit kernel */
-    CG_PATH_PIPELINE = 3   /* comb geometries (N = 10 P Q, teeth at +-r mod 10):
-                              fast readout and register-resident fit over chunks
-                              on two plan-owned streams, so memory streaming and
-                              fitting overlap */
+    CG_PATH_PIPELINE = 3   /* readout kernel (the pruned comb transform when the
+                              geometry admits it and the frames are 4-byte
+                              aligned, else the general transform), then the
+                              initial-guess and fit kernels, over chunks on two
+                              plan-owned streams */
 };
 
 /* Options of a plan.  Fill with cg_opts_default() and change what you need. */

@@ -220,9 +220,10 @@ cudaError_t setup_fit_kernels(cg_plan_s* p)
 {
     p->fit_ok = false;
     const int T = p->T;
-    // LM lanes per frame: one lane per frame for T <= 100 (no reductions),
-    // else 4 or 8 lanes with shuffle reductions
-    int G = p->opts.lanes_per_frame ? p->opts.lanes_per_frame : (T <= 100 ? 1 : (T <= 112 ? 4 : 8));
+    // LM lanes per frame (measured on GB300): one lane per frame for small T
+    // (no reductions), two lanes for T <= 100 (twice the resident frames at
+    // one shuffle level), else 8 lanes with shuffle reductions
+    int G = p->opts.lanes_per_frame ? p->opts.lanes_per_frame : (T <= 48 ? 1 : (T <= 100 ? 2 : 8));
     bool exact = false;
     int ppl = cg::fit2_ppl(G, T, &exact);
     while (ppl == 0 && G < 32 && !p->opts.lanes_per_frame) ppl = cg::fit2_ppl(G *= 2, T, &exact);
@@ -580,9 +581,9 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         free_plan(p);
         return cuda_fail(e, "throughput path set-up");
     }
-    if (o.init == CG_INIT_MLP && (!p->fit_ok || (o.readout == CG_READOUT_FFT && !p->fast_ok) || T > 256)) {
+    if (o.init == CG_INIT_MLP && (!p->fit_ok || T > 256)) {
         free_plan(p);
-        return fail(CG_ERR_UNSUPPORTED, "the learned initial guess needs the pipelined path and n_teeth <= 256");
+        return fail(CG_ERR_UNSUPPORTED, "the learned initial guess needs the fit kernels and n_teeth <= 256");
     }
     *out = p;
     return CG_OK;
@@ -614,8 +615,9 @@ cg_status cg_plan_describe(cg_plan_t p, cg_plan_info* info, int* bins_host)
     info->frames_per_cta = p->F;
     info->lanes_per_frame = p->G;
     info->n_collisions = p->n_collisions;
-    info->path = (p->opts.path == CG_PATH_AUTO) ? (p->fast_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED)
-               : (p->opts.path == CG_PATH_PIPELINE && !p->fast_ok) ? CG_PATH_FUSED : p->opts.path;
+    info->path = (p->opts.path == CG_PATH_AUTO) ? (p->fit_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED)
+               : (p->opts.path == CG_PATH_PIPELINE && !p->fit_ok) ? CG_PATH_FUSED : p->opts.path;
+    if (p->opts.readout == CG_READOUT_GEMM_SPLIT || p->opts.init == CG_INIT_MLP) info->path = CG_PATH_PIPELINE;
     if (info->path == CG_PATH_PIPELINE) info->lanes_per_frame = p->G2;
     if (bins_host) std::memcpy(bins_host, p->bins.data(), sizeof(int) * p->T);
     return CG_OK;
@@ -656,14 +658,13 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
     const bool mlp = p->opts.init == CG_INIT_MLP;
     if (mlp && !p->mlp_ok) return fail(CG_ERR_STATE, "init is CG_INIT_MLP but no network is loaded (cg_mlp_load)");
     int path = p->opts.path;
-    if (path == CG_PATH_AUTO) path = p->fast_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED;
-    // the fast readout reads sample pairs as 32-bit words: frames 4-byte aligned
-    if (path == CG_PATH_PIPELINE && (!p->fast_ok || (reinterpret_cast<uintptr_t>(frames) & 3)))
-        path = CG_PATH_FUSED;
+    if (path == CG_PATH_AUTO) path = p->fit_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED;
+    if (path == CG_PATH_PIPELINE && !p->fit_ok) path = CG_PATH_FUSED;
     // tensor-core readout or learned guess: readout, then guess and fit kernels
     if (gemm || mlp) path = CG_PATH_PIPELINE;
-    if (mlp && !gemm && (reinterpret_cast<uintptr_t>(frames) & 3))
-        return fail(CG_ERR_ARG, "frames_dev must be 4-byte aligned with the learned initial guess");
+    // the fast readout reads sample pairs as 32-bit words (frames 4-byte
+    // aligned); otherwise the pipeline reads out with the general transform
+    const bool fast = !gemm && p->fast_ok && !(reinterpret_cast<uintptr_t>(frames) & 3);
     if (path == CG_PATH_PIPELINE) {
         const int64_t cmax = n < p->chunk ? n : p->chunk;
         if (mlp && p->d.fb_cap < cmax) {
@@ -693,8 +694,9 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
             int16_t* ic = iters ? iters + c0 : nullptr;
             int16_t* sc = status ? status + c0 : nullptr;
             e = timed(p, CG_STAGE_READOUT, p->s_read, [&] {
-                return gemm ? cg::launch_gemm_readout(p, fc, m, ac, yc, p->s_read)
-                            : cg::launch_fast_readout(p, fc, m, ac, yc, p->s_read);
+                return gemm   ? cg::launch_gemm_readout(p, fc, m, ac, yc, p->s_read)
+                       : fast ? cg::launch_fast_readout(p, fc, m, ac, yc, p->s_read)
+                              : cg::launch_readout(p, fc, m, ac, yc, p->s_read);
             });
             if (e == cudaSuccess && mlp)
                 e = timed(p, CG_STAGE_MLP, p->s_read, [&] { return cg::launch_mlp(p, yc, ac, m, pc, sc, p->s_read); });

@@ -572,6 +572,9 @@ static const Fit2Inst kFit2[] = {
     {16, 13, true, fit2_fn<16, 13, true>}, {16, 14, true, fit2_fn<16, 14, true>},
     {32, 1, true, fit2_fn<32, 1, true>},   {32, 4, true, fit2_fn<32, 4, true>},
     {32, 7, true, fit2_fn<32, 7, true>},
+    {4, 56, true, fit2_fn<4, 56, true>},   {4, 51, true, fit2_fn<4, 51, true>},
+    {2, 24, false, fit2_fn<2, 24, false>}, {2, 32, false, fit2_fn<2, 32, false>},
+    {2, 50, false, fit2_fn<2, 50, false>},
     {4, 8, false, fit2_fn<4, 8, false>},   {4, 16, false, fit2_fn<4, 16, false>},
     {4, 32, false, fit2_fn<4, 32, false>}, {8, 8, false, fit2_fn<8, 8, false>},
     {8, 16, false, fit2_fn<8, 16, false>}, {8, 32, false, fit2_fn<8, 32, false>},
