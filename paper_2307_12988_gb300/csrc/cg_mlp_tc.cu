@@ -189,29 +189,69 @@ __global__ void __launch_bounds__(kMlpThreads, 2) mlp_infer_kernel(const __grid_
         const float* src = (a.y ? a.y : a.amps) + f0 * T;
         const float* in_mean = tab + kMlpTabIn;
         const float* in_scale = in_mean + T;
-        // the tile's rows are contiguous: one flat coalesced sweep with eight
-        // loads in flight per thread, (row, tooth) tracked incrementally
+        // the tile's rows are contiguous (and 16-byte aligned when the array
+        // is, since a tile starts at a multiple of 128 rows): one flat
+        // coalesced sweep, eight loads in flight per thread, (row, tooth)
+        // tracked incrementally
         constexpr int kE = kEpiWarps * 32;
         const int total = rows * T;
-        int r = tid / T, k = tid - (tid / T) * T;
-        for (int e0 = 0; e0 < total; e0 += 8 * kE) {
-            float v[8];
+        auto put = [&](float v, int r, int k) {
+            float x = a.y ? v : __fmul_rn(v, __ldg(a.inv_ref + k));
+            x = (x - in_mean[k]) * in_scale[k];
+            *reinterpret_cast<__nv_bfloat16*>(Abuf + a_off(r, k)) = __float2bfloat16_rn(x);
+        };
+        if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+            const float4* src4 = reinterpret_cast<const float4*>(src);
+            const int total4 = total >> 2;
+            const int qT = (4 * kE) / T, rT = (4 * kE) - qT * T;   // one step of 4 kE elements
+            int r = (4 * tid) / T, k = 4 * tid - r * T;
+            for (int j0 = 0; j0 < total4; j0 += 8 * kE) {
+                float4 v[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int e = e0 + q * kE + tid;
-                v[q] = e < total ? __ldcs(src + e) : 0.f;
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (e0 + q * kE + tid < total) {
-                    float x = a.y ? v[q] : __fmul_rn(v[q], __ldg(a.inv_ref + k));
-                    x = (x - in_mean[k]) * in_scale[k];
-                    *reinterpret_cast<__nv_bfloat16*>(Abuf + a_off(r, k)) = __float2bfloat16_rn(x);
+                for (int q = 0; q < 8; ++q) {
+                    const int j = j0 + q * kE + tid;
+                    v[q] = j < total4 ? __ldcs(src4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                k += kE;
-                while (k >= T) {
-                    k -= T;
-                    ++r;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (j0 + q * kE + tid < total4) {
+                        const float e4[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+                        int rr = r, kk = k;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            put(e4[i], rr, kk);
+                            if (++kk == T) {
+                                kk = 0;
+                                ++rr;
+                            }
+                        }
+                    }
+                    r += qT;
+                    k += rT;
+                    if (k >= T) {
+                        k -= T;
+                        ++r;
+                    }
+                }
+            }
+            for (int e = 4 * total4 + tid; e < total; e += kE) put(src[e], e / T, e - (e / T) * T);
+        } else {
+            int r = tid / T, k = tid - (tid / T) * T;
+            for (int e0 = 0; e0 < total; e0 += 8 * kE) {
+                float v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int e = e0 + q * kE + tid;
+                    v[q] = e < total ? __ldcs(src + e) : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (e0 + q * kE + tid < total) put(v[q], r, k);
+                    k += kE;
+                    while (k >= T) {
+                        k -= T;
+                        ++r;
+                    }
                 }
             }
         }
@@ -241,21 +281,28 @@ __global__ void __launch_bounds__(kMlpThreads, 2) mlp_infer_kernel(const __grid_
         tc::tc_fence_after();
         if (ok) {
             unsigned char* rbase = Abuf + row * 128;
-            for (int cb = half * 8; cb < half * 8 + 8; ++cb) {
-                float v[16];
-                tc::tmem_ld16(lane_base + 16 * cb, v);
-                uint32_t w[8];
+            for (int cp = half * 4; cp < half * 4 + 4; ++cp) {
+                // 32 columns per TMEM wait
+                uint32_t raw[2][16];
+                tc::tmem_ld16_async(lane_base + 32 * cp, raw[0]);
+                tc::tmem_ld16_async(lane_base + 32 * cp + 16, raw[1]);
+                tc::tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int c = cb * 16 + 2 * i;
-                    w[i] = pack_bf16(gelu_fast(v[2 * i] + tab[kMlpTabB1 + c]),
-                                     gelu_fast(v[2 * i + 1] + tab[kMlpTabB1 + c + 1]));
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int cb = 2 * cp + hh;
+                    uint32_t w[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int c = cb * 16 + 2 * i;
+                        w[i] = pack_bf16(gelu_fast(__uint_as_float(raw[hh][2 * i]) + tab[kMlpTabB1 + c]),
+                                         gelu_fast(__uint_as_float(raw[hh][2 * i + 1]) + tab[kMlpTabB1 + c + 1]));
+                    }
+                    unsigned char* base = rbase + (cb >> 2) * (kMM * 128);
+                    const int c16 = (cb & 3) * 2;
+                    *reinterpret_cast<uint4*>(base + ((c16 ^ (row & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<uint4*>(base + (((c16 + 1) ^ (row & 7)) << 4)) =
+                        make_uint4(w[4], w[5], w[6], w[7]);
                 }
-                unsigned char* base = rbase + (cb >> 2) * (kMM * 128);
-                const int c16 = (cb & 3) * 2;
-                *reinterpret_cast<uint4*>(base + ((c16 ^ (row & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
-                *reinterpret_cast<uint4*>(base + (((c16 + 1) ^ (row & 7)) << 4)) =
-                    make_uint4(w[4], w[5], w[6], w[7]);
             }
         }
         tc::tc_fence_before();
@@ -274,13 +321,15 @@ __global__ void __launch_bounds__(kMlpThreads, 2) mlp_infer_kernel(const __grid_
         tc::tc_fence_after();
         float o[4] = {0.f, 0.f, 0.f, 0.f};
         if (ok) {
-            for (int cb = half * 8; cb < half * 8 + 8; ++cb) {
-                float v[16];
-                tc::tmem_ld16(lane_base + 16 * cb, v);
+            for (int cp = half * 4; cp < half * 4 + 4; ++cp) {
+                uint32_t raw[2][16];
+                tc::tmem_ld16_async(lane_base + 32 * cp, raw[0]);
+                tc::tmem_ld16_async(lane_base + 32 * cp + 16, raw[1]);
+                tc::tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int c = cb * 16 + i;
-                    const float h = gelu_fast(v[i] + tab[kMlpTabB2 + c]);
+                for (int i = 0; i < 32; ++i) {
+                    const int c = cp * 32 + i;
+                    const float h = gelu_fast(__uint_as_float(raw[i >> 4][i & 15]) + tab[kMlpTabB2 + c]);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) o[j] = fmaf(tab[kMlpTabW3 + j * kHid + c], h, o[j]);
                 }
