@@ -306,6 +306,225 @@ __global__ void __launch_bounds__(192, 1) dft_gemm_kernel(const __grid_constant_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Decoupled rings (12-bit samples, at most 256 output columns per tile):
+// samples and twiddles go through separate mbarrier rings, so the sample ring
+// can be deep (a.stages K blocks) while the twiddle ring holds kSB stages.
+// HALVES = 1: 128-frame tiles, K blocks alternating over two accumulators
+// (TMEM columns 0 and 256) that are summed at the end; HALVES = 2: 256-frame
+// tiles whose two 128-frame halves share every twiddle stage, one
+// accumulator per half.
+//   warps 0 .. 4H-1  stage the samples (cp.async, in-place FP16) and run the
+//                    epilogue (TMEM lane quarter w % 4, half w / 4);
+//   warp 4H          TMA-loads the W_hi / W_lo tiles;
+//   warp 4H+1        owns TMEM and issues tcgen05.mma from one lane.
+// ---------------------------------------------------------------------------
+constexpr int kSB = 2;       // twiddle stages (2 x NT x 128 B each)
+constexpr int kSAMax = 8;    // sample stages at most
+
+template <int HALVES>
+__global__ void __launch_bounds__((4 * HALVES + 2) * 32, 1) dft_gemm_ring_kernel(const __grid_constant__ CUtensorMap tmB,
+                                                                                 GemmArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char gsm_raw[];
+    unsigned char* gsm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    constexpr int kLoaders = 128 * HALVES;
+    const int NT = a.ntile;
+    const int SA = a.stages;
+    const int a_half = kBM * kBK * 2;            // 16 KiB: one 128-frame half of a K block
+    const int a_stage = HALVES * a_half;
+    const int b_bytes = NT * kBK * 2;            // one (hi or lo) twiddle tile
+    const int b_stage = 2 * b_bytes;
+    unsigned char* Aring = gsm;
+    unsigned char* Bring = gsm + SA * a_stage;   // a_stage is a multiple of 1024
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(Bring + kSB * b_stage);
+    uint64_t* emptyA = fullA + kSAMax;
+    uint64_t* fullB = emptyA + kSAMax;
+    uint64_t* emptyB = fullB + kSB;
+    uint64_t* done = emptyB + kSB;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t m0 = static_cast<int64_t>(blockIdx.x) * (HALVES * kBM);
+    const int nt = blockIdx.y;
+    const int nkb = a.nkb;
+    constexpr int kTmaWarp = 4 * HALVES, kMmaWarp = 4 * HALVES + 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SA; ++s) {
+            tc::mbar_init(&fullA[s], kLoaders);   // every sample loader
+            tc::mbar_init(&emptyA[s], 1);         // one MMA commit
+        }
+        for (int s = 0; s < kSB; ++s) {
+            tc::mbar_init(&fullB[s], 1);          // the TMA issuer's expect_tx arrival
+            tc::mbar_init(&emptyB[s], 1);
+        }
+        tc::mbar_init(done, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == kMmaWarp) tc::tmem_alloc(tmem_slot, 512);
+    if (warp == kTmaWarp && lane == 0) tc::prefetch_tmap(&tmB);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < kTmaWarp) {
+        // ---------------- sample loaders (cp.async D = SA - 2 blocks ahead) ----
+        const int t = threadIdx.x & 127;
+        const int half = threadIdx.x >> 7;
+        const int rsub = t >> 4;            // row within a pass of 8 rows
+        const int c4 = t & 15;              // group of 4 samples
+        auto piece_off = [&](int pass) {
+            const int r = pass * 8 + rsub;
+            return half * a_half + r * 128 + (((c4 >> 1) ^ (r & 7)) << 4) + ((c4 & 1) << 3);
+        };
+        // two stages of slack: the block being converted and the block the
+        // tensor core reads, so issuing never waits on the latest MMA
+        const int D = SA - 2 > 0 ? SA - 2 : 1;
+        auto issue = [&](int kb) {
+            if (kb < nkb && !*abort_flag) {
+                const int s = kb % SA;
+                if (wait_or_abort(&emptyA[s], ((kb / SA) & 1u) ^ 1u, abort_flag)) {
+                    unsigned char* As = Aring + s * a_stage;
+                    const int k = kb * kBK + 4 * c4;
+#pragma unroll
+                    for (int pass = 0; pass < kBM / 8; ++pass) {
+                        const int64_t f = m0 + half * kBM + pass * 8 + rsub;
+                        const bool in = (f < a.n) && (k < a.N);
+                        const int16_t* src = in ? a.frames + f * a.N + k : a.frames;
+                        tc::cp_async8_zfill(As + piece_off(pass), src, in ? 8u : 0u);
+                    }
+                } else {
+                    *abort_flag = 1;
+                }
+            }
+            tc::cp_async_commit();   // one group per K block, possibly empty
+        };
+        for (int j = 0; j < D; ++j) issue(j);
+        for (int kb = 0; kb < nkb; ++kb) {
+            issue(kb + D);
+            tc::cp_async_wait_pending(D > 3 ? 3 : D);
+            if (D > 3) asm volatile("cp.async.wait_group 4;\n" ::: "memory");
+            if (*abort_flag) break;
+            unsigned char* As = Aring + (kb % SA) * a_stage;
+#pragma unroll
+            for (int pass = 0; pass < kBM / 8; ++pass) {
+                const int off = piece_off(pass);
+                const uint2 w = *reinterpret_cast<const uint2*>(As + off);
+                __half h[4];
+                h[0] = __short2half_rn(static_cast<short>(w.x & 0xffffu));
+                h[1] = __short2half_rn(static_cast<short>(w.x >> 16));
+                h[2] = __short2half_rn(static_cast<short>(w.y & 0xffffu));
+                h[3] = __short2half_rn(static_cast<short>(w.y >> 16));
+                *reinterpret_cast<uint2*>(As + off) = *reinterpret_cast<const uint2*>(h);
+            }
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&fullA[kb % SA]);
+        }
+        tc::cp_async_wait_pending(0);
+    } else if (warp == kTmaWarp) {
+        // ---------------- twiddle tiles by TMA ----------------
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % kSB;
+                if (!wait_or_abort(&emptyB[s], ((kb / kSB) & 1u) ^ 1u, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                unsigned char* Bs = Bring + s * b_stage;
+                tc::mbar_arrive_expect_tx(&fullB[s], static_cast<uint32_t>(b_stage));
+                tc::tma_load_2d(Bs, &tmB, kb * kBK, nt * NT, &fullB[s]);
+                tc::tma_load_2d(Bs + b_bytes, &tmB, kb * kBK, a.nrows_total + nt * NT, &fullB[s]);
+                issued = kb + 1;
+            }
+            for (int kb = issued - kSB > 0 ? issued - kSB : 0; kb < issued; ++kb)
+                (void)tc::mbar_wait(&fullB[kb % kSB], (kb / kSB) & 1u, kMaxPolls);
+        }
+    } else {
+        // ---------------- MMA issue ----------------
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_f16(kBM, NT, 0);
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int sa = kb % SA, sb = kb % kSB;
+                if (!wait_or_abort(&fullA[sa], (kb / SA) & 1u, abort_flag) ||
+                    !wait_or_abort(&fullB[sb], (kb / kSB) & 1u, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t abase = tc::smem_u32(Aring + sa * a_stage);
+                const uint32_t bh = tc::smem_u32(Bring + sb * b_stage);
+                const uint32_t bl = bh + b_bytes;
+#pragma unroll
+                for (int h = 0; h < HALVES; ++h) {
+                    // HALVES = 2: accumulator of half h; HALVES = 1: K blocks alternate
+                    const int acc = HALVES == 2 ? h : (kb & 1);
+                    const uint32_t d = tmem + static_cast<uint32_t>(acc * 256);
+                    const bool first = HALVES == 2 ? (kb == 0) : (kb < 2);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint32_t koff = kk * 32;
+                        const uint64_t ad = tc::sdesc_sw128(abase + h * a_half + koff);
+                        tc::mma_f16(d, ad, tc::sdesc_sw128(bh + koff), idesc, (!first || kk != 0) ? 1u : 0u);
+                        tc::mma_f16(d, ad, tc::sdesc_sw128(bl + koff), idesc, 1);
+                    }
+                }
+                tc::mma_commit(&emptyA[sa]);
+                tc::mma_commit(&emptyB[sb]);
+            }
+            tc::mma_commit(done);   // also on abort, so TMEM is quiescent before it is freed
+        }
+    }
+
+    if (warp < kTmaWarp) {
+        // ---------------- epilogue: TMEM -> |X| -> amps (and y) ----------------
+        const bool ok = wait_or_abort(done, 0, abort_flag) && !*abort_flag;
+        __syncwarp();
+        tc::tc_fence_after();
+        if (ok) {
+            const int quarter = warp & 3, half = warp >> 2;
+            const int64_t f = m0 + half * kBM + quarter * 32 + lane;
+            const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
+            const int teeth_tile = NT / 2;
+            for (int j = 0; j < NT / 16; ++j) {
+                float v[16];
+                tc::tmem_ld16(lane_base + static_cast<uint32_t>(half * 256) + 16 * j, v);
+                if (HALVES == 1 && nkb > 1) {
+                    float w[16];
+                    tc::tmem_ld16(lane_base + 256 + 16 * j, w);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += w[i];
+                }
+                if (f < a.n) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int tooth = nt * teeth_tile + 8 * j + i;
+                        if (tooth < a.T) {
+                            const float amp = sqrtf(fmaf(v[2 * i], v[2 * i], v[2 * i + 1] * v[2 * i + 1]));
+                            if (a.amps) a.amps[f * a.T + tooth] = amp;
+                            if (a.y) a.y[f * a.T + tooth] = __fmul_rn(amp, a.inv_ref[tooth]);
+                        }
+                    }
+                }
+            }
+        } else if (threadIdx.x == 0) {
+            atomicExch(a.err, 1);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -392,6 +611,28 @@ cudaError_t setup_gemm(cg_plan_s* p)
     g.stages = stages;
     p->gemm_smem = 1024 + stages * stage_bytes + 8 * (3 * kPipeMax + 1) + 16;
     p->gemm_ntiles = ntiles;
+    // decoupled-ring kernel: 12-bit samples, NT <= 256; 256-frame tiles (one
+    // accumulator per half) only while FP32 accumulation over N samples stays
+    // well within the error bound, else 128-frame tiles alternating two
+    // accumulators; as many sample stages as shared memory holds
+    p->gemm_ring = !split && NT <= 256 && N <= 4096;
+    if (p->gemm_ring) {
+        p->gemm_halves = (N <= 1536) ? 2 : 1;
+        const int a_stage = p->gemm_halves * a_bytes;
+        const int fixed = 1024 + kSB * 2 * b_bytes + 8 * (2 * kSAMax + 2 * kSB + 1) + 16;
+        int sa = (227 * 1024 - fixed) / a_stage;
+        if (sa > kSAMax) sa = kSAMax;
+        if (sa < 3) {
+            p->gemm_ring = false;
+        } else {
+            p->gemm_ring_stages = sa;
+            p->gemm_ring_smem = fixed + sa * a_stage;
+            void* rk = p->gemm_halves == 2 ? reinterpret_cast<void*>(&dft_gemm_ring_kernel<2>)
+                                           : reinterpret_cast<void*>(&dft_gemm_ring_kernel<1>);
+            cudaError_t e2 = raise_smem_limit(rk, p->gemm_ring_smem);
+            if (e2 != cudaSuccess) return e2;
+        }
+    }
     void* fn = split ? reinterpret_cast<void*>(&dft_gemm_kernel<true>) : reinterpret_cast<void*>(&dft_gemm_kernel<false>);
     return raise_smem_limit(fn, p->gemm_smem);
 }
@@ -405,6 +646,15 @@ cudaError_t launch_gemm_readout(const cg_plan_s* p, const int16_t* frames, int64
     g.amps = amps;
     g.y = y;
     g.vec8 = (reinterpret_cast<uintptr_t>(frames) & 7) == 0 && (p->N % 4) == 0;
+    if (p->gemm_ring && g.vec8) {
+        const int H = p->gemm_halves;
+        g.stages = p->gemm_ring_stages;
+        dim3 grid2(static_cast<unsigned>((n + H * kBM - 1) / (H * kBM)), static_cast<unsigned>(p->gemm_ntiles));
+        void* args2[] = {const_cast<CUtensorMap*>(&p->gemm_map), &g};
+        void* rk = H == 2 ? reinterpret_cast<void*>(&dft_gemm_ring_kernel<2>)
+                          : reinterpret_cast<void*>(&dft_gemm_ring_kernel<1>);
+        return cudaLaunchKernel(rk, grid2, dim3((4 * H + 2) * 32), args2, p->gemm_ring_smem, s);
+    }
     dim3 grid(static_cast<unsigned>((n + kBM - 1) / kBM), static_cast<unsigned>(p->gemm_ntiles));
     void* fn = p->gemm_split_x ? reinterpret_cast<void*>(&dft_gemm_kernel<true>)
                                : reinterpret_cast<void*>(&dft_gemm_kernel<false>);

@@ -199,6 +199,8 @@ struct cg_plan_s {
     // split-precision GEMM readout
     CUtensorMap gemm_map{};
     int gemm_split_x = 1, gemm_smem = 0, gemm_ntiles = 0;
+    bool gemm_ring = false;  // decoupled-ring kernel (12-bit samples, NT <= 256)
+    int gemm_halves = 1, gemm_ring_stages = 0, gemm_ring_smem = 0;
     int solve_f64 = 0;
     cg::GemmArgs ga{};
     int Q = 0;               // L = 10 Q
