@@ -220,10 +220,19 @@ cudaError_t setup_fit_kernels(cg_plan_s* p)
 {
     p->fit_ok = false;
     const int T = p->T;
-    // LM lanes per frame (measured on GB300): one lane per frame for small T
-    // (no reductions), two lanes for T <= 100 (twice the resident frames at
-    // one shuffle level), else 8 lanes with shuffle reductions
-    int G = p->opts.lanes_per_frame ? p->opts.lanes_per_frame : (T <= 48 ? 1 : (T <= 100 ? 2 : 8));
+    // LM lanes per frame (measured on GB300).  FP32 solve: one lane per frame
+    // for small T (no reductions), two lanes for T <= 100 (twice the resident
+    // frames at one shuffle level), else four (eight beyond the instantiated
+    // point counts).  FP64 solve: the solve's long dependent FP64 chain runs
+    // once per lane group, so fewer lanes per frame (more frames per warp)
+    // win: one lane for T <= 100, else four.
+    int G = p->opts.lanes_per_frame;
+    if (G == 0) {
+        if (p->solve_f64)
+            G = T <= 100 ? 1 : 4;
+        else
+            G = T <= 48 ? 1 : (T <= 100 ? 2 : 4);
+    }
     bool exact = false;
     int ppl = cg::fit2_ppl(G, T, &exact);
     while (ppl == 0 && G < 32 && !p->opts.lanes_per_frame) ppl = cg::fit2_ppl(G *= 2, T, &exact);
