@@ -104,6 +104,25 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest x over the ranks of the process group (x itself with one
+    rank): every rank's work is timed, the job is as slow as its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(frames_per_rank: int, world_size: int, seconds: float) -> float:
+    """Whole-job throughput: every rank processes its own frames_per_rank
+    frames (no collective on the data path), the job takes the slowest
+    rank's time."""
+    return frames_per_rank * world_size / seconds
+
+
 GEOMETRIES = {
     # name: (synth geometry attribute, generator keywords)
     "paper_rate": ("PAPER_RATE", dict(snr_db=30.0, center_amp_hz=20e6)),
@@ -278,11 +297,7 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
     ms_step = ms / args.steps
 
     # per-kernel timing pass (events on the launching streams), after the
@@ -303,7 +318,7 @@ def run_ours(args):
     dominant = max(kern, key=lambda k: kern[k]["launches"] * kern[k]["ms_per_launch"])
     dom = kern[dominant]
     total_frames = n * ws
-    value = total_frames / (ms_step / 1e3)
+    value = weak_scaling_value(n, ws, ms_step / 1e3)
     achieved = bytes_per_frame * n / (ms_step / 1e3) / 1e9
     result = {
         "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": ws,
@@ -392,13 +407,9 @@ def run_e2e(plan, frames_dev, n, T, dev, args, ws):
     for _ in range(steps):
         one_pass()
     torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / steps
-    if ws > 1:
-        t = torch.tensor([dt], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks((time.perf_counter() - t0) / steps, dev)
     d2h = n * (4 * T + 16 + 4 + 2 + 2)
-    return {"value": n * ws / dt, "unit": "spectra/s", "h2d_bytes_per_step": n * N * 2,
+    return {"value": weak_scaling_value(n, ws, dt), "unit": "spectra/s", "h2d_bytes_per_step": n * N * 2,
             "d2h_bytes_per_step": d2h, "chunk_frames": chunk, "steps": steps,
             "input_gbs": n * ws * N * 2 / dt / 1e9}
 
