@@ -216,6 +216,54 @@ struct OddEvenNet {
 // then computes its frame's guess exactly as the oracle defines it: baseline
 // = median of the outer fifth (sorted with the network, +inf padding), sign
 // of the largest deviation, centroid / extreme / area of the one-signed excess.
+// Moment initial guess from the baseline B0 (the median of the outer teeth):
+// d = y - B0, s = sign of the largest |d|, w = max(s d, 0); c0 = centroid of
+// w over the abscissa, A0 = s max w, g0 = area / (pi |A0|) clamped to
+// [du / 2, span / 2]; a flat spectrum gives c0 = u_mid and a flag.  y(k)
+// returns tooth k's normalised value, u(k) its abscissa.  Shared by the
+// initial-guess kernel and the readout that fuses it, so both give the same
+// bits.
+template <class Y, class U>
+__device__ __forceinline__ void moment_finish(Y y, U u, int T, float B0, float u_mid, float du, float span,
+                                              float x_mid, float x_scale, float* po, int16_t* flag_out)
+{
+    float best = -1.f;
+    int bestk = 0;
+    for (int k = 0; k < T; ++k) {
+        const float dv = fabsf(y(k) - B0);
+        if (dv > best) {
+            best = dv;
+            bestk = k;
+        }
+    }
+    const float sgn = (y(bestk) - B0) >= 0.f ? 1.0f : -1.0f;
+    float W = 0.f, Wu = 0.f, wmax = 0.f;
+    for (int k = 0; k < T; ++k) {
+        const float w = fmaxf(sgn * (y(k) - B0), 0.f);
+        W += w;
+        Wu = fmaf(w, u(k), Wu);
+        wmax = fmaxf(wmax, w);
+    }
+    float c0, g0, A0;
+    int flag = 0;
+    if (!(W > 0.f)) {
+        c0 = u_mid;
+        g0 = 0.5f * du;
+        A0 = 0.f;
+        flag = kInitFlat;
+    } else {
+        A0 = sgn * wmax;
+        g0 = W * du / (3.14159265358979f * fabsf(A0));
+        g0 = fminf(fmaxf(g0, 0.5f * du), 0.5f * span);
+        c0 = Wu / W;
+    }
+    po[0] = fmaf(x_scale, c0, x_mid);
+    po[1] = x_scale * g0;
+    po[2] = A0;
+    po[3] = B0;
+    if (flag_out) *flag_out = static_cast<int16_t>(flag);
+}
+
 template <int NPAD>
 __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
 {
@@ -298,39 +346,8 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
                 vhi = (i == rhi) ? v[i] : vhi;
             }
             const float B0 = 0.5f * (vlo + vhi);
-            float best = -1.f;
-            int bestk = 0;
-            for (int k = 0; k < T; ++k) {
-                const float dv = fabsf(r[k] - B0);
-                if (dv > best) { best = dv; bestk = k; }
-            }
-            const float sgn = (r[bestk] - B0) >= 0.f ? 1.0f : -1.0f;
-            float W = 0.f, Wu = 0.f, wmax = 0.f;
-            for (int k = 0; k < T; ++k) {
-                const float w = fmaxf(sgn * (r[k] - B0), 0.f);
-                W += w;
-                Wu = fmaf(w, us[k], Wu);
-                wmax = fmaxf(wmax, w);
-            }
-            float c0, g0, A0;
-            int flag = 0;
-            if (!(W > 0.f)) {
-                c0 = a.u_mid;
-                g0 = 0.5f * a.du;
-                A0 = 0.f;
-                flag = kInitFlat;
-            } else {
-                A0 = sgn * wmax;
-                g0 = W * a.du / (3.14159265358979f * fabsf(A0));
-                g0 = fminf(fmaxf(g0, 0.5f * a.du), 0.5f * a.span);
-                c0 = Wu / W;
-            }
-            float* po = a.p0_out + fo * 4;
-            po[0] = fmaf(a.x_scale, c0, a.x_mid);
-            po[1] = a.x_scale * g0;
-            po[2] = A0;
-            po[3] = B0;
-            if (a.flag_out) a.flag_out[fo] = static_cast<int16_t>(flag);
+            moment_finish([&](int k) { return r[k]; }, [&](int k) { return us[k]; }, T, B0, a.u_mid, a.du, a.span,
+                          a.x_mid, a.x_scale, a.p0_out + fo * 4, a.flag_out ? a.flag_out + fo : nullptr);
         }
         __syncwarp();
     }

@@ -57,8 +57,6 @@ struct FastArgs {
     const float* u;          // [T]
     float* amps;             // [n][T] or null
     float* y;                // [n][T] or null
-    float* p0_out;           // [n][4] starting parameters (abscissa units)
-    int16_t* flag_out;       // [n] initial-guess flags, or null
     int sm_twL, sm_twN, sm_tom, sm_iref, sm_u, sm_raw, sm_Y, sm_amps, sm_y, sm_total;
 };
 
