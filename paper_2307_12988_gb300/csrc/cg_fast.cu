@@ -34,6 +34,11 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -365,6 +370,13 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
     const int T = a.T;
     float* us = fsm;
     float* iref = fsm + T;
+    // per lane a slot of PPL points (odd stride: conflict-free) for the
+    // group's next frame, copied asynchronously while the current one is fit
+    // (G >= 4; with fewer lanes the points take most registers and the next
+    // frame's loads go straight to registers when it starts)
+    constexpr bool kPrefetch = G >= 4;
+    constexpr int kSlot = PPL | 1;
+    float* const slot = kPrefetch ? fsm + 2 * T + static_cast<int>(threadIdx.x) * kSlot : nullptr;
     for (int i = threadIdx.x; i < T; i += blockDim.x) {
         us[i] = a.u[i];
         iref[i] = a.inv_ref[i];
@@ -381,7 +393,8 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
         n = c < n ? c : n;
     }
 
-    int64_t f = -1, fr = -1;     // task index, frame index
+    int64_t f = -1, fr = -1;     // task index, frame index being fit
+    int64_t fn = -1, frn = -1;   // the group's next frame (copy in flight)
     float yv[PPL];
 #pragma unroll
     for (int j = 0; j < PPL; ++j) yv[j] = 0.f;
@@ -396,8 +409,9 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
     bool fresh = false;
 
     while (true) {
-        // ---- hand frames to idle groups (all lanes of a group agree) ----
-        unsigned need = __ballot_sync(kFull, gl == 0 && f < 0);
+        // ---- hand frames to groups (a group's lanes agree): with prefetch a
+        //      group claims its next frame while fitting the current one ----
+        unsigned need = __ballot_sync(kFull, gl == 0 && (kPrefetch ? fn < 0 : f < 0));
         while (need != 0 && next < n) {
             if (next >= end) {
                 unsigned long long t = 0;
@@ -415,31 +429,25 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
             const int take = static_cast<int>(avail < cnt ? avail : cnt);
             const int rank = __popc(need & ((1u << leader_lane) - 1u));
             if (((need >> leader_lane) & 1u) && rank < take) {
-                f = next + rank;
-                fresh = true;
+                if constexpr (kPrefetch) {
+                    fn = next + rank;
+                    frn = a.list ? static_cast<int64_t>(a.list[fn]) : fn;
+                    const float* src = (a.y ? a.y : a.amps) + frn * T;
+#pragma unroll
+                    for (int j = 0; j < PPL; ++j) {
+                        const int k = gl + G * j;
+                        if (k < T) cp_async4(slot + j, src + k);
+                    }
+                } else {
+                    f = next + rank;
+                    fresh = true;
+                }
             }
             next += take;
-            need = __ballot_sync(kFull, gl == 0 && f < 0);
+            need = __ballot_sync(kFull, gl == 0 && (kPrefetch ? fn < 0 : f < 0));
         }
-        if (!__any_sync(kFull, f >= 0)) break;
-
-        if (fresh) {
-            fr = a.list ? static_cast<int64_t>(a.list[f]) : f;
-            if (a.y) {
-                const float* src = a.y + fr * T;
-#pragma unroll
-                for (int j = 0; j < PPL; ++j) {
-                    const int k = gl + G * j;
-                    yv[j] = (k < T) ? src[k] : 0.f;
-                }
-            } else {
-                const float* src = a.amps + fr * T;
-#pragma unroll
-                for (int j = 0; j < PPL; ++j) {
-                    const int k = gl + G * j;
-                    yv[j] = (k < T) ? __fmul_rn(src[k], iref[k]) : 0.f;
-                }
-            }
+        // p, flag, lambda and counters of a frame that starts now
+        auto start_frame = [&]() {
             const float* q = a.p0 + fr * 4;
             p[0] = (q[0] - a.x_mid) * inv_scale;
             p[1] = q[1] * inv_scale;
@@ -449,6 +457,45 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
             lambda = a.lambda0;
             it = 0;
             st = kMaxIter;
+        };
+        if constexpr (kPrefetch) {
+            cp_async_commit();
+            // a group with no current frame starts its next one
+            if (f < 0 && fn >= 0) {
+                f = fn;
+                fr = frn;
+                fn = frn = -1;
+                fresh = true;
+                cp_async_wait_all();
+#pragma unroll
+                for (int j = 0; j < PPL; ++j) {
+                    const int k = gl + G * j;
+                    yv[j] = (k < T) ? (a.y ? slot[j] : __fmul_rn(slot[j], iref[k])) : 0.f;
+                }
+                start_frame();
+            }
+            if (!__any_sync(kFull, f >= 0 || fn >= 0)) break;
+        } else {
+            if (!__any_sync(kFull, f >= 0)) break;
+            if (fresh) {
+                fr = a.list ? static_cast<int64_t>(a.list[f]) : f;
+                if (a.y) {
+                    const float* src = a.y + fr * T;
+#pragma unroll
+                    for (int j = 0; j < PPL; ++j) {
+                        const int k = gl + G * j;
+                        yv[j] = (k < T) ? src[k] : 0.f;
+                    }
+                } else {
+                    const float* src = a.amps + fr * T;
+#pragma unroll
+                    for (int j = 0; j < PPL; ++j) {
+                        const int k = gl + G * j;
+                        yv[j] = (k < T) ? __fmul_rn(src[k], iref[k]) : 0.f;
+                    }
+                }
+                start_frame();
+            }
         }
         // ---- trial point ----
         float pe[4] = {p[0], p[1], p[2], p[3]};
@@ -539,6 +586,7 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
             f = -1;
         }
     }
+    if constexpr (kPrefetch) cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -718,9 +766,12 @@ cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, i
 
 size_t fit2_smem(int G, int T)
 {
-    // G == 1: abscissa table, 4 warps x [2][32] row slots, 4 x 32 slot offsets
-    return G == 1 ? sizeof(float) * (T + 4 * 64 * (T | 1)) + sizeof(int) * 4 * 32
-                  : sizeof(float) * 2 * T;
+    // G == 1: abscissa table, 4 warps x [2][32] row slots, 4 x 32 slot offsets;
+    // G > 1: abscissa and 1 / reference tables, one PPL slot per thread
+    if (G == 1) return sizeof(float) * (T + 4 * 64 * (T | 1)) + sizeof(int) * 4 * 32;
+    bool exact = false;
+    const int ppl = fit2_ppl(G, T, &exact);
+    return sizeof(float) * (2 * T + (G >= 4 ? static_cast<size_t>(fit2_threads(G)) * (ppl | 1) : 0));
 }
 
 }  // namespace cg
