@@ -309,22 +309,62 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
             // incrementally
             const float* src = (a.y ? a.y : a.amps) + f0 * T;
             const int total = nf * T;
-            int f = lane / T, k = lane - (lane / T) * T;
-            for (int e0 = 0; e0 < total; e0 += 8 * 32) {
-                float v[8];
+            auto put = [&](float v, int f, int k) { rows[f * TS + k] = a.y ? v : __fmul_rn(v, iref[k]); };
+            if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+                // 16-byte loads (a task starts at a multiple of 32 rows, so
+                // the block is aligned whenever the array is)
+                const float4* src4 = reinterpret_cast<const float4*>(src);
+                const int total4 = total >> 2;
+                const int qT = 128 / T, rT = 128 - qT * T;   // one step of 32 lanes x 4 values
+                int f = (4 * lane) / T, k = 4 * lane - ((4 * lane) / T) * T;
+                for (int j0 = 0; j0 < total4; j0 += 8 * 32) {
+                    float4 v[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int e = e0 + q * 32 + lane;
-                    v[q] = e < total ? src[e] : 0.f;
+                    for (int q = 0; q < 8; ++q) {
+                        const int jj = j0 + q * 32 + lane;
+                        v[q] = jj < total4 ? src4[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (j0 + q * 32 + lane < total4) {
+                            const float e4[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+                            int ff = f, kk = k;
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                put(e4[i], ff, kk);
+                                if (++kk == T) {
+                                    kk = 0;
+                                    ++ff;
+                                }
+                            }
+                        }
+                        f += qT;
+                        k += rT;
+                        if (k >= T) {
+                            k -= T;
+                            ++f;
+                        }
+                    }
                 }
+                for (int e = 4 * total4 + lane; e < total; e += 32) put(src[e], e / T, e - (e / T) * T);
+            } else {
+                int f = lane / T, k = lane - (lane / T) * T;
+                for (int e0 = 0; e0 < total; e0 += 8 * 32) {
+                    float v[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int e = e0 + q * 32 + lane;
-                    if (e < total) rows[f * TS + k] = a.y ? v[q] : __fmul_rn(v[q], iref[k]);
-                    k += 32;
-                    while (k >= T) {
-                        k -= T;
-                        ++f;
+                    for (int q = 0; q < 8; ++q) {
+                        const int e = e0 + q * 32 + lane;
+                        v[q] = e < total ? src[e] : 0.f;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int e = e0 + q * 32 + lane;
+                        if (e < total) put(v[q], f, k);
+                        k += 32;
+                        while (k >= T) {
+                            k -= T;
+                            ++f;
+                        }
                     }
                 }
             }
