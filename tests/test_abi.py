@@ -76,3 +76,50 @@ def test_null_arguments_rejected():
     assert lib.cg_process(None, None, 0, None, None, None, None, None, None, None) == 1
     assert lib.cg_fit(None, None, 1, None, None, None, None, None, None) == 1
     assert lib.cg_plan_describe(None, None, None) == 1
+
+
+def test_new_entry_points_reject_bad_arguments_before_cuda():
+    """Argument checks of the learned-guess, streaming and timing entry points
+    answer without touching the device."""
+    import ctypes
+    lib = cg.load()
+    h = ctypes.c_void_p()
+    # network shapes and batch limits
+    assert lib.cg_mlp_create(ctypes.byref(h), 0, 256, 4, 16, 1) == 1
+    assert lib.cg_mlp_create(ctypes.byref(h), 221, 2000, 4, 16, 1) == 1
+    assert lib.cg_mlp_create(ctypes.byref(h), 221, 256, 0, 16, 1) == 1
+    assert lib.cg_mlp_create(ctypes.byref(h), 221, 256, 4, 0, 1) == 1
+    assert lib.cg_mlp_create(None, 221, 256, 4, 16, 1) == 1
+    assert cg.cg_mlp_param_count(221, 256, 4) == 256 * 221 + 256 + 256 * 256 + 256 + 4 * 256 + 4
+    assert cg.cg_mlp_param_count(0, 256, 4) == 0
+    assert lib.cg_mlp_forward(None, None, 1, None, None) == 1
+    assert lib.cg_mlp_backward(None, None, None, 1, None, None, None) == 1
+    assert lib.cg_mlp_adam(None, ctypes.c_float(1e-3), ctypes.c_float(0.9), ctypes.c_float(0.999),
+                           ctypes.c_float(1e-8), None) == 1
+    assert lib.cg_mlp_load(None, None, 0) == 1
+    assert lib.cg_mlp_infer(None, None, 1, None, None) == 1
+    size = ctypes.c_size_t()
+    assert lib.cg_mlp_save(None, None, 0, ctypes.byref(size)) == 1
+    # streaming
+    assert lib.cg_server_create(ctypes.byref(h), 0) == 1
+    assert lib.cg_server_create(None, 1 << 20) == 1
+    assert lib.cg_server_inject(None, 1, 0.0) == 1
+    assert lib.cg_stream_create(ctypes.byref(h), None, None, 1 << 20, 16, 1e-3, 100) == 1
+    assert lib.cg_stream_push(None, None, 1, 0, -1.0) == 1
+    n = ctypes.c_int64()
+    assert lib.cg_stream_poll(None, None, None, 1, ctypes.byref(n), 0.0) == 1
+    assert lib.cg_stream_flush(None, 0.0) == 1
+    assert lib.cg_stream_destroy(None) == 0          # NULL is ignored
+    assert lib.cg_server_destroy(None) == 0
+    # timing
+    assert lib.cg_timing_enable(None, 1) == 1
+    assert lib.cg_timing_collect(None, None, None) == 1
+    assert cg.cg_clock() > 0
+
+
+@pytest.mark.parametrize("kw", [dict(init=7), dict(polish_iter=-1)])
+def test_plan_rejects_bad_learned_options(kw):
+    opts = cg.cg_opts_default(**kw)
+    with pytest.raises(cg.CgError) as ei:
+        cg.cg_plan(1e9, 1000, np.array([11e6, 21e6, 31e6, 41e6, 51e6]), None, None, opts)
+    assert ei.value.status == 1
