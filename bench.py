@@ -184,7 +184,7 @@ def kernel_rooflines(stage_ms, stage_launches, n, g, T, args, mean_iters, hbm, b
         per = ms / cnt / 1e3                       # s per launch
         frames = n * args.steps_timed / cnt
         r = {"launches": cnt, "ms_per_launch": per * 1e3}
-        if st == "readout" and args.readout == "fft":
+        if st == "readout" and args.readout in ("fft", "fold"):
             b = (2 * g.frame_len + 4 * T) * frames
             r.update(bound="hbm", achieved=b / per / 1e9, peak=hbm, unit="GB/s")
         elif st == "readout":
@@ -260,7 +260,8 @@ def run_ours(args):
     del ref_frames
     plan = cg.Plan(g.sample_rate, g.frame_len, g.tooth_freqs, g.tooth_x, ref,
                    lanes_per_frame=args.lanes, path=args.path, chunk_frames=args.chunk,
-                   readout=(cg.READOUT_GEMM_SPLIT if args.readout == "gemm" else cg.READOUT_FFT),
+                   readout={"fft": cg.READOUT_FFT, "gemm": cg.READOUT_GEMM_SPLIT,
+                            "fold": cg.READOUT_FOLD_GEMM}[args.readout],
                    sample_bits=args.sample_bits,
                    init=(cg.INIT_MLP if args.init == "mlp" else cg.INIT_MOMENT),
                    polish_iter=args.polish)
@@ -566,7 +567,10 @@ def main():
     ap.add_argument("--path", type=int, default=0, help="0 auto, 1 fused, 2 split, 3 pipeline")
     ap.add_argument("--chunk", type=int, default=0, help="frames per pipelined chunk (0: default)")
     ap.add_argument("--workload", choices=sorted(GEOMETRIES), default="paper_rate")
-    ap.add_argument("--readout", choices=["fft", "gemm"], default="fft")
+    ap.add_argument("--readout", choices=["fft", "gemm", "fold"], default="fft",
+                    help="fft: pruned transform on the CUDA cores; gemm: DFT-at-teeth product on the "
+                         "tensor cores; fold: coset fold on the CUDA cores + DFT at the teeth on the "
+                         "tensor cores")
     ap.add_argument("--init", choices=["moment", "mlp"], default="moment",
                     help="initial guess; mlp loads the trained network (221 teeth)")
     ap.add_argument("--polish", type=int, default=0, help="LM polish steps after the MLP guess (0: 2)")

@@ -60,7 +60,15 @@ typedef enum cg_status {
                                  did not converge; the frame was refit by the full LM
                                  from the moment initial guess */
 
-enum { CG_READOUT_FFT = 0, CG_READOUT_GEMM_SPLIT = 1 };
+/* Tooth readout.  FFT: the pruned (coset) or general shared-memory transform
+   on the CUDA cores.  GEMM_SPLIT: X at the tooth bins as one dense product
+   [frames x N] . [N x 2 teeth] on the tensor cores (FP16 samples, FP16 hi + lo
+   twiddles, FP32 accumulation).  FOLD_GEMM: radix-10 coset geometries only
+   (N = 10 L, L even, every tooth bin = +-r mod 10, at most 128 teeth): each
+   frame is folded to L complex values on the CUDA cores, then the L-point DFT
+   at the teeth is a split-precision (hi + lo) product on the tensor cores;
+   frames that are not 4-byte aligned are read out by the general transform. */
+enum { CG_READOUT_FFT = 0, CG_READOUT_GEMM_SPLIT = 1, CG_READOUT_FOLD_GEMM = 2 };
 enum { CG_FFT_AUTO = 0, CG_FFT_FULL = 1, CG_FFT_COSET = 2 };
 enum { CG_INIT_MOMENT = 0, CG_INIT_MLP = 1 };
 /* Kernel arrangement of cg_process. */
@@ -77,7 +85,8 @@ enum {
 
 /* Options of a plan.  Fill with cg_opts_default() and change what you need. */
 typedef struct cg_opts {
-    int readout;          /* CG_READOUT_FFT (default) */
+    int readout;          /* CG_READOUT_FFT (default), CG_READOUT_GEMM_SPLIT or
+                             CG_READOUT_FOLD_GEMM */
     int fft;              /* CG_FFT_AUTO: coset-pruned transform when every tooth bin
                              lies in one residue pair +-r mod M (M | N), else full */
     int init;             /* CG_INIT_MOMENT (default) */

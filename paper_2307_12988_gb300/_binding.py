@@ -28,7 +28,7 @@ FIT_FALLBACK = 0x20
 STAGE_READOUT, STAGE_INIT, STAGE_MLP, STAGE_FIT, STAGE_FALLBACK, STAGE_FUSED = 0, 1, 2, 3, 4, 5
 N_STAGES = 8
 STAGE_NAMES = {0: "readout", 1: "init", 2: "mlp", 3: "fit", 4: "fallback", 5: "fused"}
-READOUT_FFT, READOUT_GEMM_SPLIT = 0, 1
+READOUT_FFT, READOUT_GEMM_SPLIT, READOUT_FOLD_GEMM = 0, 1, 2
 FFT_AUTO, FFT_FULL, FFT_COSET = 0, 1, 2
 INIT_MOMENT, INIT_MLP = 0, 1
 PATH_AUTO, PATH_FUSED, PATH_SPLIT, PATH_PIPELINE = 0, 1, 2, 3

@@ -121,6 +121,7 @@ void free_tables(cg::DevTables& d)
     cudaFree(d.tooth_of_m);
     cudaFree(d.fit_counter);
     cudaFree(d.gemm_W);
+    cudaFree(d.fold_W);
     cudaFree(d.err);
     cudaFree(d.mlp_W);
     cudaFree(d.mlp_tab);
@@ -391,8 +392,8 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         return fail(CG_ERR_ARG, "lanes_per_frame must be 0, 1, 2, 4, 8, 16 or 32");
     if (o.path < CG_PATH_AUTO || o.path > CG_PATH_PIPELINE) return fail(CG_ERR_ARG, "path must be a CG_PATH_* value");
     if (o.chunk_frames < 0) return fail(CG_ERR_ARG, "chunk_frames must be >= 0");
-    if (o.readout != CG_READOUT_FFT && o.readout != CG_READOUT_GEMM_SPLIT)
-        return fail(CG_ERR_ARG, "readout must be CG_READOUT_FFT or CG_READOUT_GEMM_SPLIT");
+    if (o.readout != CG_READOUT_FFT && o.readout != CG_READOUT_GEMM_SPLIT && o.readout != CG_READOUT_FOLD_GEMM)
+        return fail(CG_ERR_ARG, "readout must be CG_READOUT_FFT, CG_READOUT_GEMM_SPLIT or CG_READOUT_FOLD_GEMM");
     if (o.sample_bits != 12 && o.sample_bits != 16) return fail(CG_ERR_ARG, "sample_bits must be 12 or 16");
     if (o.solve_f64 < -1 || o.solve_f64 > 1) return fail(CG_ERR_ARG, "solve_f64 must be -1, 0 or 1");
     if (o.init != CG_INIT_MOMENT && o.init != CG_INIT_MLP) return fail(CG_ERR_ARG, "init must be CG_INIT_MOMENT or CG_INIT_MLP");
@@ -590,6 +591,18 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         free_plan(p);
         return cuda_fail(e, "throughput path set-up");
     }
+    if (o.readout == CG_READOUT_FOLD_GEMM) {
+        if ((e = cg::setup_fold(p, zidx)) != cudaSuccess) {
+            free_plan(p);
+            return cuda_fail(e, "folded tensor-core readout set-up");
+        }
+        if (!p->fold_ok || !p->fit_ok) {
+            free_plan(p);
+            return fail(CG_ERR_UNSUPPORTED,
+                        "the folded tensor-core readout needs a radix-10 coset geometry with even L = N / 10, "
+                        "n_teeth <= 128 and the fit kernels");
+        }
+    }
     if (o.init == CG_INIT_MLP && (!p->fit_ok || T > 256)) {
         free_plan(p);
         return fail(CG_ERR_UNSUPPORTED, "the learned initial guess needs the fit kernels and n_teeth <= 256");
@@ -626,7 +639,7 @@ cg_status cg_plan_describe(cg_plan_t p, cg_plan_info* info, int* bins_host)
     info->n_collisions = p->n_collisions;
     info->path = (p->opts.path == CG_PATH_AUTO) ? (p->fit_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED)
                : (p->opts.path == CG_PATH_PIPELINE && !p->fit_ok) ? CG_PATH_FUSED : p->opts.path;
-    if (p->opts.readout == CG_READOUT_GEMM_SPLIT || p->opts.init == CG_INIT_MLP) info->path = CG_PATH_PIPELINE;
+    if (p->opts.readout != CG_READOUT_FFT || p->opts.init == CG_INIT_MLP) info->path = CG_PATH_PIPELINE;
     if (info->path == CG_PATH_PIPELINE) info->lanes_per_frame = p->G2;
     if (bins_host) std::memcpy(bins_host, p->bins.data(), sizeof(int) * p->T);
     return CG_OK;
@@ -665,15 +678,17 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
     cudaError_t e;
     const bool gemm = p->opts.readout == CG_READOUT_GEMM_SPLIT;
     const bool mlp = p->opts.init == CG_INIT_MLP;
+    // both comb readouts read sample pairs as 32-bit words (frames 4-byte
+    // aligned); otherwise the pipeline reads out with the general transform
+    const bool aligned4 = !(reinterpret_cast<uintptr_t>(frames) & 3);
+    const bool fold = p->opts.readout == CG_READOUT_FOLD_GEMM && p->fold_ok && aligned4;
     if (mlp && !p->mlp_ok) return fail(CG_ERR_STATE, "init is CG_INIT_MLP but no network is loaded (cg_mlp_load)");
     int path = p->opts.path;
     if (path == CG_PATH_AUTO) path = p->fit_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED;
     if (path == CG_PATH_PIPELINE && !p->fit_ok) path = CG_PATH_FUSED;
-    // tensor-core readout or learned guess: readout, then guess and fit kernels
-    if (gemm || mlp) path = CG_PATH_PIPELINE;
-    // the fast readout reads sample pairs as 32-bit words (frames 4-byte
-    // aligned); otherwise the pipeline reads out with the general transform
-    const bool fast = !gemm && p->fast_ok && !(reinterpret_cast<uintptr_t>(frames) & 3);
+    // tensor-core readouts or learned guess: readout, then guess and fit kernels
+    if (p->opts.readout != CG_READOUT_FFT || mlp) path = CG_PATH_PIPELINE;
+    const bool fast = !gemm && !fold && p->fast_ok && aligned4;
     if (path == CG_PATH_PIPELINE) {
         const int64_t cmax = n < p->chunk ? n : p->chunk;
         if (mlp && p->d.fb_cap < cmax) {
@@ -704,6 +719,7 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
             int16_t* sc = status ? status + c0 : nullptr;
             e = timed(p, CG_STAGE_READOUT, p->s_read, [&] {
                 return gemm   ? cg::launch_gemm_readout(p, fc, m, ac, yc, p->s_read)
+                       : fold ? cg::launch_fold_readout(p, fc, m, ac, yc, p->s_read)
                        : fast ? cg::launch_fast_readout(p, fc, m, ac, yc, p->s_read)
                               : cg::launch_readout(p, fc, m, ac, yc, p->s_read);
             });
@@ -771,8 +787,11 @@ cg_status cg_readout(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
     if (!amps && !y) return fail(CG_ERR_ARG, "amps_dev and y_dev are both NULL");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
+    const bool aligned4 = !(reinterpret_cast<uintptr_t>(frames) & 3);
     if (p->opts.readout == CG_READOUT_GEMM_SPLIT)
         e = cg::launch_gemm_readout(p, frames, n, amps, y, s);
+    else if (p->opts.readout == CG_READOUT_FOLD_GEMM && p->fold_ok && aligned4)
+        e = cg::launch_fold_readout(p, frames, n, amps, y, s);
     else if (p->fast_ok && (p->opts.path == CG_PATH_AUTO || p->opts.path == CG_PATH_PIPELINE) &&
              !(reinterpret_cast<uintptr_t>(frames) & 3))
         e = cg::launch_fast_readout(p, frames, n, amps, y, s);

@@ -146,8 +146,33 @@ struct GemmArgs {
     int* err;                // set to nonzero by a block whose bounded wait ran out
 };
 
+// Arguments of the folded DFT-at-teeth readout on the tensor cores
+// (cg_fold_gemm.cu): the radix-10 coset fold on the CUDA cores, then the
+// L-point DFT at the teeth as a split-precision product on the tensor cores.
+struct FoldArgs {
+    const int16_t* frames;
+    int64_t n;
+    int N, T, L;
+    int nkb;                 // K blocks of 32 FP16 elements (16 fold outputs, Re/Im)
+    int ntile;               // output columns (2 per tooth), multiple of 16, <= 256
+    int acc_stride;          // TMEM columns between the two accumulators
+    int tmem_cols;           // TMEM columns allocated per block
+    int stages;              // A ring stages
+    float c1, s1, c2, s2;    // W_10^(r j) for j = 1, 2
+    float z_scale;           // fold outputs are scaled by this power of two before FP16
+    float out_scale;         // 1 / z_scale, applied to |X|
+    const float2* twN;       // [L] W_N^(r m)
+    const float* inv_ref;    // [T]
+    float* amps;             // [n][T] or null
+    float* y;                // [n][T] or null
+    int* err;
+    // shared-memory layout (byte offsets from the 1024-byte-aligned base)
+    int sm_W, sm_A, sm_stage, sm_tw, sm_iref, sm_bar, sm_total;
+};
+
 struct DevTables {
     void* gemm_W = nullptr;       // [2][rows][Kpad] FP16 twiddles (hi, lo)
+    void* fold_W = nullptr;       // [2][ntile][Kpad] FP16 twiddles of the folded readout
     int* err = nullptr;           // device-side error word
     float2* tw_M5 = nullptr;
     int* tooth_of_m = nullptr;
@@ -197,6 +222,11 @@ struct cg_plan_s {
     // split-precision GEMM readout
     CUtensorMap gemm_map{};
     int gemm_split_x = 1, gemm_smem = 0, gemm_ntiles = 0;
+    bool fold_ok = false;    // folded tensor-core readout configured
+    CUtensorMap fold_map{};
+    cg::FoldArgs fo{};
+    int grid_fold = 0;
+    int fold_sign = 1;       // (-1)^r of the coset fold
     bool gemm_ring = false;  // decoupled-ring kernel (12-bit samples, NT <= 256)
     int gemm_halves = 1, gemm_ring_stages = 0, gemm_ring_smem = 0;
     int solve_f64 = 0;
@@ -280,6 +310,11 @@ cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, i
 cudaError_t setup_mlp(cg_plan_s* p, const unsigned char* blob, size_t bytes, const char** why);
 cudaError_t launch_mlp(const cg_plan_s* p, const float* y, const float* amps, int64_t n, float* p0,
                        int16_t* flags, cudaStream_t s);
+
+// folded DFT-at-teeth readout on the tensor cores (cg_fold_gemm.cu)
+cudaError_t setup_fold(cg_plan_s* p, const std::vector<int>& zidx);
+cudaError_t launch_fold_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps, float* y,
+                                cudaStream_t s);
 
 // split-precision GEMM readout (cg_gemm.cu)
 cudaError_t setup_gemm(cg_plan_s* p);

@@ -90,6 +90,11 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* m
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
+// bring [p, p + bytes) into L2 without waiting (p and bytes multiples of 16)
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map)
 {
     asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
@@ -170,6 +175,18 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t smem_addr)
     d |= static_cast<uint64_t>((1024u >> 4) & 0x3FFFu) << 32;   // SBO = 1024 B
     d |= static_cast<uint64_t>(1u) << 46;                 // descriptor version
     d |= static_cast<uint64_t>(2u) << 61;                 // SWIZZLE_128B
+    return d;
+}
+// The same for rows of 32 16-bit elements (64 B) with 64-byte swizzle:
+// 8-row atoms of 512 B (stride byte offset), layout 4.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t smem_addr)
+{
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((smem_addr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>(1u) << 16;
+    d |= static_cast<uint64_t>((512u >> 4) & 0x3FFFu) << 32;    // SBO = 512 B
+    d |= static_cast<uint64_t>(1u) << 46;
+    d |= static_cast<uint64_t>(4u) << 61;                 // SWIZZLE_64B
     return d;
 }
 // Instruction descriptor, kind::f16: FP32 accumulator, A and B FP16 (fmt 0)
