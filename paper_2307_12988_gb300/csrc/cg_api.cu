@@ -254,7 +254,8 @@ cudaError_t setup_fit_kernels(cg_plan_s* p)
     ia.x_mid = static_cast<float>(p->x_mid);
     ia.x_scale = static_cast<float>(p->x_scale);
     p->init_npad = npad;
-    p->init_smem = 4 * (2 * T + p->n_outer) + 4 * 4 * 32 * ia.row_stride;
+    // tables, 2 mbarriers and 2 x 32 staged rows per warp (4 warps)
+    p->init_smem = 4 * ((2 * T + p->n_outer + 3) & ~3) + 8 * 2 * 4 + 4 * 4 * 2 * 32 * ia.row_stride;
     cudaError_t e;
     int occ = 0;
     void* ff = cg::fit2_ptr(G, ppl, exact);
@@ -264,6 +265,10 @@ cudaError_t setup_fit_kernels(cg_plan_s* p)
     if ((e = cudaMalloc(&p->d.fit_counter, sizeof(unsigned long long))) != cudaSuccess) return e;
     if (occ < 1) return cudaSuccess;
     p->grid_fit2 = p->num_sms * occ;
+    if (!p->d.err) {
+        if ((e = cudaMalloc(&p->d.err, sizeof(int))) != cudaSuccess) return e;
+        if ((e = cudaMemset(p->d.err, 0, sizeof(int))) != cudaSuccess) return e;
+    }
     void* fi = cg::init_ptr(npad);
     if ((e = cg::raise_smem_limit(fi, p->init_smem)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fi, 128, p->init_smem)) != cudaSuccess) return e;

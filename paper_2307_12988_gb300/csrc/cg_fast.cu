@@ -26,6 +26,7 @@
 #include "cg_fft.cuh"
 #include "cg_fit.cuh"
 #include "cg_internal.h"
+#include "cg_tc.cuh"
 
 namespace cg {
 
@@ -216,39 +217,39 @@ struct OddEvenNet {
     }
 };
 
-// A warp stages the normalised spectra of 32 consecutive frames (row stride
-// odd, so the lanes' reads of one tooth fall on distinct banks); each lane
-// then computes its frame's guess exactly as the oracle defines it: baseline
-// = median of the outer fifth (sorted with the network, +inf padding), sign
-// of the largest deviation, centroid / extreme / area of the one-signed excess.
 // Moment initial guess from the baseline B0 (the median of the outer teeth):
 // d = y - B0, s = sign of the largest |d|, w = max(s d, 0); c0 = centroid of
 // w over the abscissa, A0 = s max w, g0 = area / (pi |A0|) clamped to
 // [du / 2, span / 2]; a flat spectrum gives c0 = u_mid and a flag.  y(k)
-// returns tooth k's normalised value, u(k) its abscissa.  Shared by the
-// initial-guess kernel and the readout that fuses it, so both give the same
-// bits.
+// returns tooth k's normalised value, u(k) its abscissa.
 template <class Y, class U>
 __device__ __forceinline__ void moment_finish(Y y, U u, int T, float B0, float u_mid, float du, float span,
                                               float x_mid, float x_scale, float* po, int16_t* flag_out)
 {
+    // one pass: the extreme deviation and the excess sums of both signs (the
+    // sign picks one set at the end; each sum sees the same terms in the same
+    // order as a second pass would)
     float best = -1.f;
-    int bestk = 0;
+    float dbest = y(0) - B0;
+    float Wp = 0.f, Wup = 0.f, wmaxp = 0.f, Wn = 0.f, Wun = 0.f, wmaxn = 0.f;
     for (int k = 0; k < T; ++k) {
-        const float dv = fabsf(y(k) - B0);
+        const float d = y(k) - B0;
+        const float dv = fabsf(d);
         if (dv > best) {
             best = dv;
-            bestk = k;
+            dbest = d;
         }
+        const float wp = fmaxf(d, 0.f), wn = fmaxf(-d, 0.f);
+        const float uk = u(k);
+        Wp += wp;
+        Wup = fmaf(wp, uk, Wup);
+        wmaxp = fmaxf(wmaxp, wp);
+        Wn += wn;
+        Wun = fmaf(wn, uk, Wun);
+        wmaxn = fmaxf(wmaxn, wn);
     }
-    const float sgn = (y(bestk) - B0) >= 0.f ? 1.0f : -1.0f;
-    float W = 0.f, Wu = 0.f, wmax = 0.f;
-    for (int k = 0; k < T; ++k) {
-        const float w = fmaxf(sgn * (y(k) - B0), 0.f);
-        W += w;
-        Wu = fmaf(w, u(k), Wu);
-        wmax = fmaxf(wmax, w);
-    }
+    const float sgn = dbest >= 0.f ? 1.0f : -1.0f;
+    const float W = sgn > 0.f ? Wp : Wn, Wu = sgn > 0.f ? Wup : Wun, wmax = sgn > 0.f ? wmaxp : wmaxn;
     float c0, g0, A0;
     int flag = 0;
     if (!(W > 0.f)) {
@@ -269,6 +270,13 @@ __device__ __forceinline__ void moment_finish(Y y, U u, int T, float B0, float u
     if (flag_out) *flag_out = static_cast<int16_t>(flag);
 }
 
+// A warp takes 32 consecutive frames at a time: their normalised spectra
+// (row stride odd, so the lanes' reads of one tooth fall on distinct banks)
+// arrive in shared memory by one bulk copy per 32 rows, double-buffered so the
+// next rows land while these are read (else by coalesced loads); each lane
+// then computes its frame's guess as the oracle defines it: baseline = median
+// of the outer fifth (sorted with the network, +inf padding), sign of the
+// largest deviation, centroid / extreme / area of the one-signed excess.
 template <int NPAD>
 __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
 {
@@ -277,14 +285,24 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
     float* us = ism;
     float* iref = us + T;
     int* outer = reinterpret_cast<int*>(iref + T);
-    float* rows = reinterpret_cast<float*>(outer + a.n_outer) + (threadIdx.x >> 5) * 32 * TS;
+    // per warp two mbarriers and two 32-row buffers (task t lands in buffer
+    // t % 2 while the other one is read)
+    const int warp = threadIdx.x >> 5;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ism + ((2 * T + a.n_outer + 3) & ~3)) + 2 * warp;
+    float* rows0 = reinterpret_cast<float*>(reinterpret_cast<uint64_t*>(ism + ((2 * T + a.n_outer + 3) & ~3)) + 8) +
+                   warp * 2 * 32 * TS;
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        tc::mbar_init(&bars[0], 1);
+        tc::mbar_init(&bars[1], 1);
+        tc::fence_mbar_init();
+    }
     for (int i = threadIdx.x; i < T; i += blockDim.x) {
         us[i] = a.u[i];
         iref[i] = a.inv_ref[i];
     }
     for (int i = threadIdx.x; i < a.n_outer; i += blockDim.x) outer[i] = a.outer_idx[i];
     __syncthreads();
-    const int lane = threadIdx.x & 31;
     constexpr OddEvenNet<NPAD> net{};
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
     int64_t n = a.n;
@@ -292,22 +310,58 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
         const int64_t c = *a.list_n;
         n = c < n ? c : n;
     }
-    for (int64_t task = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-         task * 32 < n; task += nwarps) {
+    const float* srcbase = a.y ? a.y : a.amps;
+    // a whole task of 32 contiguous rows goes by one bulk copy (16-byte
+    // aligned: 32 rows of odd T floats are 128 T bytes)
+    auto bulk_ok = [&](int64_t task) {
+        return a.bulk && !a.list && (task + 1) * 32 <= n &&
+               (reinterpret_cast<uintptr_t>(srcbase + task * 32 * T) & 15) == 0;
+    };
+    auto issue = [&](int64_t task, int b) {
+        if (lane == 0) {
+            tc::fence_proxy_async_smem();   // generic reads of the buffer are ordered before the copy
+            tc::mbar_arrive_expect_tx(&bars[b], static_cast<uint32_t>(32 * T * 4));
+            tc::bulk_g2s(rows0 + b * 32 * TS, srcbase + task * 32 * T, static_cast<uint32_t>(32 * T * 4), &bars[b]);
+        }
+    };
+    uint32_t phase = 0u, pending = 0u;   // bit b: buffer b's parity / a copy in flight
+    int64_t task = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + warp;
+    if (task * 32 < n && bulk_ok(task)) {
+        issue(task, 0);
+        pending |= 1u;
+    }
+    bool failed = false;
+    for (int b = 0; task * 32 < n; task += nwarps, b ^= 1) {
+        float* rows = rows0 + b * 32 * TS;
         const int64_t f0 = task * 32;
         const int nf = (n - f0) < 32 ? static_cast<int>(n - f0) : 32;
-        if (a.list) {
+        // the next task's copy goes out before this one is read
+        const int64_t nt = task + nwarps;
+        __syncwarp();
+        if (nt * 32 < n && bulk_ok(nt)) {
+            issue(nt, b ^ 1);
+            pending |= 1u << (b ^ 1);
+        }
+        const bool in_smem_raw = (pending >> b) & 1u;   // rows hold y, or amps still to be scaled
+        if (in_smem_raw) {
+            if (!tc::mbar_wait(&bars[b], (phase >> b) & 1u, 1u << 24)) {
+                failed = true;
+                break;
+            }
+            phase ^= 1u << b;
+            pending &= ~(1u << b);
+        } else if (a.list) {
             // listed frames (the fallback pass): one coalesced row at a time
             for (int f = 0; f < nf; ++f) {
                 const int64_t fr = a.list[f0 + f];
-                const float* src = (a.y ? a.y : a.amps) + fr * T;
+                const float* src = srcbase + fr * T;
                 for (int k = lane; k < T; k += 32) rows[f * TS + k] = a.y ? src[k] : __fmul_rn(src[k], iref[k]);
             }
         } else {
             // the 32 rows are contiguous in global memory: one flat coalesced
             // sweep, eight loads in flight per lane, (frame, tooth) tracked
             // incrementally
-            const float* src = (a.y ? a.y : a.amps) + f0 * T;
+            const float* src = srcbase + f0 * T;
             const int total = nf * T;
             auto put = [&](float v, int f, int k) { rows[f * TS + k] = a.y ? v : __fmul_rn(v, iref[k]); };
             if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
@@ -373,9 +427,12 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
         if (lane < nf) {
             const int64_t fo = a.list ? static_cast<int64_t>(a.list[f0 + lane]) : f0 + lane;
             const float* r = rows + lane * TS;
+            // bulk-copied magnitudes are normalised here, as the staging does
+            const bool scale = in_smem_raw && !a.y;
+            auto yk = [&](int k) { return scale ? __fmul_rn(r[k], iref[k]) : r[k]; };
             float v[NPAD];
 #pragma unroll
-            for (int i = 0; i < NPAD; ++i) v[i] = (i < a.n_outer) ? r[outer[i]] : INFINITY;
+            for (int i = 0; i < NPAD; ++i) v[i] = (i < a.n_outer) ? yk(outer[i]) : INFINITY;
 #pragma unroll
             for (int c = 0; c < OddEvenNet<NPAD>::kCount; ++c) {
                 const float lo = fminf(v[net.lo[c]], v[net.hi[c]]);
@@ -391,11 +448,15 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
                 vhi = (i == rhi) ? v[i] : vhi;
             }
             const float B0 = 0.5f * (vlo + vhi);
-            moment_finish([&](int k) { return r[k]; }, [&](int k) { return us[k]; }, T, B0, a.u_mid, a.du, a.span,
-                          a.x_mid, a.x_scale, a.p0_out + fo * 4, a.flag_out ? a.flag_out + fo : nullptr);
+            moment_finish(yk, [&](int k) { return us[k]; }, T, B0, a.u_mid, a.du, a.span, a.x_mid, a.x_scale,
+                          a.p0_out + fo * 4, a.flag_out ? a.flag_out + fo : nullptr);
         }
-        __syncwarp();
     }
+    // no copy may land after the block exits
+    __syncwarp();
+    for (int b = 0; b < 2; ++b)
+        if (((pending >> b) & 1u) && !tc::mbar_wait(&bars[b], (phase >> b) & 1u, 1u << 24)) failed = true;
+    if (failed && lane == 0 && a.err) atomicExch(a.err, 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -751,6 +812,8 @@ cudaError_t launch_init(const cg_plan_s* p, const float* y, const float* amps, i
     a.flag_out = flag_out;
     a.list = list;
     a.list_n = list_n;
+    a.bulk = (p->T & 1) ? 1 : 0;
+    a.err = p->d.err;
     const int64_t tasks = (n + 31) / 32;
     const int64_t blocks = (tasks + 3) / 4;
     const int grid = static_cast<int>(blocks < p->grid_init ? blocks : p->grid_init);

@@ -76,6 +76,8 @@ struct InitArgs {
     int16_t* flag_out;       // [n] or null
     const int* list;         // task i is frame list[i] (fallback pass), or null
     const int* list_n;       // device count of list entries, or null
+    int bulk;                // 1: whole 32-row tasks arrive by bulk copies (T odd)
+    int* err;                // device error word (a bulk copy that never landed)
 };
 
 // Arguments of the register-resident LM kernel.
