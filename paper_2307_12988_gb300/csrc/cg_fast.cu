@@ -473,9 +473,8 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
     float* iref = fsm + T;
     // per lane a slot of PPL points (odd stride: conflict-free) for the
     // group's next frame, copied asynchronously while the current one is fit
-    // (G >= 4; with fewer lanes the points take most registers and the next
-    // frame's loads go straight to registers when it starts)
-    constexpr bool kPrefetch = G >= 4;
+    // (G >= 2; one lane per frame runs the shared-memory kernel instead)
+    constexpr bool kPrefetch = G >= 2;
     constexpr int kSlot = PPL | 1;
     float* const slot = kPrefetch ? fsm + 2 * T + static_cast<int>(threadIdx.x) * kSlot : nullptr;
     for (int i = threadIdx.x; i < T; i += blockDim.x) {
@@ -870,11 +869,11 @@ cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, i
 size_t fit2_smem(int G, int T)
 {
     // G == 1: abscissa table, 4 warps x [2][32] row slots, 4 x 32 slot offsets;
-    // G > 1: abscissa and 1 / reference tables, one PPL slot per thread
+    // G > 1: abscissa and 1 / reference tables, one PPL prefetch slot per thread
     if (G == 1) return sizeof(float) * (T + 4 * 64 * (T | 1)) + sizeof(int) * 4 * 32;
     bool exact = false;
     const int ppl = fit2_ppl(G, T, &exact);
-    return sizeof(float) * (2 * T + (G >= 4 ? static_cast<size_t>(fit2_threads(G)) * (ppl | 1) : 0));
+    return sizeof(float) * (2 * T + (G >= 2 ? static_cast<size_t>(fit2_threads(G)) * (ppl | 1) : 0));
 }
 
 }  // namespace cg
