@@ -596,6 +596,10 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         free_plan(p);
         return cuda_fail(e, "throughput path set-up");
     }
+    if ((e = cg::setup_pow2(p)) != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "power-of-two readout set-up");
+    }
     if (o.readout == CG_READOUT_FOLD_GEMM) {
         if ((e = cg::setup_fold(p, zidx)) != cudaSuccess) {
             free_plan(p);
@@ -694,6 +698,7 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
     // tensor-core readouts or learned guess: readout, then guess and fit kernels
     if (p->opts.readout != CG_READOUT_FFT || mlp) path = CG_PATH_PIPELINE;
     const bool fast = !gemm && !fold && p->fast_ok && aligned4;
+    const bool pow2 = !gemm && !fold && !fast && p->pow2_ok && aligned4;
     if (path == CG_PATH_PIPELINE) {
         const int64_t cmax = n < p->chunk ? n : p->chunk;
         if (mlp && p->d.fb_cap < cmax) {
@@ -726,6 +731,7 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
                 return gemm   ? cg::launch_gemm_readout(p, fc, m, ac, yc, p->s_read)
                        : fold ? cg::launch_fold_readout(p, fc, m, ac, yc, p->s_read)
                        : fast ? cg::launch_fast_readout(p, fc, m, ac, yc, p->s_read)
+                       : pow2 ? cg::launch_pow2_readout(p, fc, m, ac, yc, p->s_read)
                               : cg::launch_readout(p, fc, m, ac, yc, p->s_read);
             });
             if (e == cudaSuccess && mlp)
@@ -797,9 +803,10 @@ cg_status cg_readout(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
         e = cg::launch_gemm_readout(p, frames, n, amps, y, s);
     else if (p->opts.readout == CG_READOUT_FOLD_GEMM && p->fold_ok && aligned4)
         e = cg::launch_fold_readout(p, frames, n, amps, y, s);
-    else if (p->fast_ok && (p->opts.path == CG_PATH_AUTO || p->opts.path == CG_PATH_PIPELINE) &&
-             !(reinterpret_cast<uintptr_t>(frames) & 3))
+    else if (p->fast_ok && (p->opts.path == CG_PATH_AUTO || p->opts.path == CG_PATH_PIPELINE) && aligned4)
         e = cg::launch_fast_readout(p, frames, n, amps, y, s);
+    else if (p->pow2_ok && (p->opts.path == CG_PATH_AUTO || p->opts.path == CG_PATH_PIPELINE) && aligned4)
+        e = cg::launch_pow2_readout(p, frames, n, amps, y, s);
     else
         e = cg::launch_readout(p, frames, n, amps, y, s);
     if (e != cudaSuccess) return cuda_fail(e, "cg_readout launch");

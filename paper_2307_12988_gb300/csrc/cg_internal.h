@@ -224,6 +224,9 @@ struct cg_plan_s {
     // split-precision GEMM readout
     CUtensorMap gemm_map{};
     int gemm_split_x = 1, gemm_smem = 0, gemm_ntiles = 0;
+    bool pow2_ok = false;    // power-of-two full-transform readout configured
+    cg::ReadoutArgs pa{};
+    int grid_pow2 = 0;
     bool fold_ok = false;    // folded tensor-core readout configured
     CUtensorMap fold_map{};
     cg::FoldArgs fo{};
@@ -312,6 +315,11 @@ cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, i
 cudaError_t setup_mlp(cg_plan_s* p, const unsigned char* blob, size_t bytes, const char** why);
 cudaError_t launch_mlp(const cg_plan_s* p, const float* y, const float* amps, int64_t n, float* p0,
                        int16_t* flags, cudaStream_t s);
+
+// power-of-two full-transform readout (cg_pow2.cu)
+cudaError_t setup_pow2(cg_plan_s* p);
+cudaError_t launch_pow2_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps, float* y,
+                                cudaStream_t s);
 
 // folded DFT-at-teeth readout on the tensor cores (cg_fold_gemm.cu)
 cudaError_t setup_fold(cg_plan_s* p, const std::vector<int>& zidx);

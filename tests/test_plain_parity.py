@@ -50,6 +50,24 @@ def test_readout_parity(dev, name, fft):
     assert np.max(np.abs(y - w["oracle"]["y"])) <= AMP_TOL
 
 
+@pytest.mark.parametrize("name", ["serve4096", "pow2_2048", "pow2_8192"])
+def test_power_of_two_readout_parity(dev, name):
+    # full real transforms with N = 2048, 4096, 8192 take the three-pass
+    # register readout on the pipeline path (4-byte aligned frames); ragged
+    # batches and a 2-byte aligned slice (general transform) as well
+    w = W.workload(name)
+    fr = torch.from_numpy(w["frames"]).to(dev)
+    n = fr.shape[0]
+    with _plan(w, path=cg.PATH_PIPELINE) as p:
+        assert p.info["fft_kind"] == cg.FFT_FULL
+        for a, b in [(0, n), (2, n - 1), (1, 40), (6, 7)]:
+            amps, y = p.readout(fr[a:b])
+            torch.cuda.synchronize()
+            err = _amp_err(amps.cpu().numpy(), {"oracle": {"amps": w["oracle"]["amps"][a:b]}, "ref": w["ref"]})
+            assert err <= AMP_TOL, (name, a, b, err)
+            assert np.max(np.abs(y.cpu().numpy() - w["oracle"]["y"][a:b])) <= AMP_TOL
+
+
 def test_coset_transform_is_chosen_for_comb_geometries():
     for name, M, L in [("tiny", 10, 100), ("paper_rate", 10, 110), ("wide", 10, 250)]:
         w = W.workload(name)

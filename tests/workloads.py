@@ -20,6 +20,9 @@ SPECS = {
     "paper_rate": (synth.PAPER_RATE, 1500, 1000, dict(snr_db=30.0, center_amp_hz=20e6)),
     "wide": (synth.WIDE, 400, 400, dict(snr_db=30.0, center_amp_hz=20e6)),
     "serve4096": (synth.SERVE_4096, 200, 300, dict(snr_db=30.0, center_amp_hz=20e6)),
+    # the other power-of-two frame lengths of the full-transform readout
+    "pow2_2048": (synth.Geometry(1.0e9, 2048, -40, 40), 300, 300, dict(snr_db=30.0, center_amp_hz=20e6)),
+    "pow2_8192": (synth.Geometry(4.0e9, 8192, -100, 100), 150, 200, dict(snr_db=30.0, center_amp_hz=20e6)),
 }
 
 
