@@ -294,6 +294,10 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_infer_kernel(const __grid_
                 tc::mbar_arrive_expect_tx(&raw_full[b], slice_bytes);
                 tc::bulk_g2s(raw + b * kSlice * 256, srcbase + (tile_f0(it) + kSlice * q) * T, slice_bytes,
                              &raw_full[b]);
+            } else {
+                // a slice read straight from global memory still completes its
+                // phase, so no thread can run two slices ahead of the others
+                tc::mbar_arrive(&raw_full[b]);
             }
             last_issued = gq;
             return true;
@@ -309,34 +313,40 @@ __global__ void __launch_bounds__(kMlpThreads, 1) mlp_infer_kernel(const __grid_
             // a bulk-copied slice is read from shared memory; a ragged or
             // unaligned one straight from global memory by each thread
             const bool bulk = bulk_ok(it, q);
-            const float* rb = bulk ? raw + b * kSlice * 256 : srcbase + (tile_f0(it) + kSlice * q) * T;
-            if (bulk && !wait_or_abort(&raw_full[b], (gq >> 1) & 1u, abort_flag)) { ok = false; break; }
+            if (!wait_or_abort(&raw_full[b], (gq >> 1) & 1u, abort_flag)) { ok = false; break; }
+            auto convert = [&](const float* rb) {
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int item = ls + 256 * j;            // 16 rows x 32 chunks of 8 teeth
-                const int r = item & (kSlice - 1), c = item >> 4;
-                const int row = kSlice * q + r;
-                uint32_t w[4] = {0u, 0u, 0u, 0u};
-                if (r < nr && c < nchunk8) {
-                    const float* src = rb + r * T + 8 * c;
+                for (int j = 0; j < 2; ++j) {
+                    const int item = ls + 256 * j;            // 16 rows x 32 chunks of 8 teeth
+                    const int r = item & (kSlice - 1), c = item >> 4;
+                    const int row = kSlice * q + r;
+                    uint32_t w[4] = {0u, 0u, 0u, 0u};
+                    if (r < nr && c < nchunk8) {
+                        const float* src = rb + r * T + 8 * c;
 #pragma unroll
-                    for (int e = 0; e < 8; e += 2) {
-                        float x2[2];
+                        for (int e = 0; e < 8; e += 2) {
+                            float x2[2];
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int k = 8 * c + e + h;
-                            float x = 0.f;
-                            if (k < T) {
-                                const float4 tk = tooth[k];
-                                x = scale_in ? __fmul_rn(src[e + h], tk.x) : src[e + h];
-                                x = (x - tk.y) * tk.z;
+                            for (int h = 0; h < 2; ++h) {
+                                const int k = 8 * c + e + h;
+                                float x = 0.f;
+                                if (k < T) {
+                                    const float4 tk = tooth[k];
+                                    x = scale_in ? __fmul_rn(src[e + h], tk.x) : src[e + h];
+                                    x = (x - tk.y) * tk.z;
+                                }
+                                x2[h] = x;
                             }
-                            x2[h] = x;
+                            w[e >> 1] = pack_bf16(x2[0], x2[1]);
                         }
-                        w[e >> 1] = pack_bf16(x2[0], x2[1]);
                     }
+                    *reinterpret_cast<uint4*>(Ain + a_off(row, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
                 }
-                *reinterpret_cast<uint4*>(Ain + a_off(row, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+            };
+            if (bulk) {
+                convert(raw + b * kSlice * 256);
+            } else {
+                convert(srcbase + (tile_f0(it) + kSlice * q) * T);
             }
             tc::mbar_arrive(&raw_empty[b]);
             if (q == nslices - 1) {

@@ -106,7 +106,10 @@ def _net_blob(n_in, seed, in_mean, in_scale, out_mean, out_scale, zero=False):
     return blob, theta
 
 
-@pytest.mark.parametrize("geom,n", [(synth.WIDE, 300), (synth.TINY, 129), (synth.PAPER_RATE, 1000)])
+# sizes with partial last tiles: whole and ragged 16-row input slices, empty
+# slices (the slices' barrier phases must stay in step)
+@pytest.mark.parametrize("geom,n", [(synth.WIDE, 300), (synth.TINY, 129), (synth.TINY, 300),
+                                    (synth.PAPER_RATE, 1000), (synth.PAPER_RATE, 2049)])
 def test_inference_kernel_matches_rounded_oracle(geom, n):
     T = geom.n_teeth
     d = synth.tooth_domain_spectra(geom, n, seed=42)
@@ -119,6 +122,7 @@ def test_inference_kernel_matches_rounded_oracle(geom, n):
     with _plan(geom, init=cg.INIT_MLP) as plan:
         plan.mlp_load(blob)
         p0 = plan.mlp_infer(_dev(y)).cpu().numpy().astype(np.float64)
+        cg.cg_check_device(plan.handle)
     xs = ((y - in_mean) * in_scale).astype(np.float32).astype(np.float64)   # FP32 like the kernel
     o = omlp.forward(theta, xs, T, 256, 4, operand_round=omlp.bf16_round)
     want = o * out_scale + out_mean
