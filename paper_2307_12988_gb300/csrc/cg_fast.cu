@@ -36,6 +36,9 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
 {
     constexpr int L = P * Q;
     constexpr int MH = 5;                     // M / 2 with M = 10
+    // long Q-point transforms: the fold runs as its own stage with one item
+    // per output (balanced over the block) and the Q-point DFTs read it back
+    constexpr bool kSplitFold = Q > 11;
     extern __shared__ __align__(16) unsigned char sm[];
     float2* twL = reinterpret_cast<float2*>(sm + a.sm_twL);
     float2* twN = reinterpret_cast<float2*>(sm + a.sm_twN);
@@ -69,15 +72,13 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
         const int nf = static_cast<int>((a.n_frames - f0) < F ? (a.n_frames - f0) : F);
         cp_async_wait_all();
         __syncthreads();
-        // ---------------- stage 1: fold, Q-point DFT, twiddle ----------------
-        for (int item = threadIdx.x; item < nf * P; item += blockDim.x) {
-            const int f = item / P;
-            const int a0 = item - f * P;
-            const int16_t* xs = raw + off + f * N + a0;
-            float2 z[Q];
-#pragma unroll
-            for (int bq = 0; bq < Q; ++bq) {
-                const int16_t* xp = xs + P * bq;
+        int offn = 0;
+        if constexpr (kSplitFold) {
+            // ---------------- stage 0: the fold, one item per output m ------
+            for (int item = threadIdx.x; item < nf * L; item += blockDim.x) {
+                const int f = item / L;
+                const int m = item - f * L;
+                const int16_t* xp = raw + off + f * N + m;
                 int D[MH];
 #pragma unroll
                 for (int j = 0; j < MH; ++j) D[j] = static_cast<int>(xp[L * j]) + sg * static_cast<int>(xp[L * (j + MH)]);
@@ -86,20 +87,60 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
                 float2 fz;
                 fz.x = fmaf(static_cast<float>(E2), c2, fmaf(static_cast<float>(E1), c1, static_cast<float>(D[0])));
                 fz.y = fmaf(static_cast<float>(F2), s2, static_cast<float>(F1) * s1);
-                z[bq] = cmul(fz, twN[a0 + P * bq]);
+                Yb[f * L + m] = cmul(fz, twN[m]);
             }
-            Dft<Q>::run(z);
-            float2* Yf = Yb + f * L + a0;
+            __syncthreads();
+            // raw is free: start the next batch's samples
+            const int64_t bn = b + gridDim.x;
+            if (bn < nb) {
+                const int nfn = static_cast<int>((a.n_frames - bn * F) < F ? (a.n_frames - bn * F) : F);
+                offn = stage_async(a.frames, bn * F * static_cast<int64_t>(N), static_cast<int64_t>(nfn) * N, raw);
+            }
+            // ---------------- stage 1: Q-point DFT over b, twiddle (in place) --
+            for (int item = threadIdx.x; item < nf * P; item += blockDim.x) {
+                const int f = item / P;
+                const int a0 = item - f * P;
+                float2* Yf = Yb + f * L + a0;
+                float2 z[Q];
 #pragma unroll
-            for (int u = 0; u < Q; ++u) Yf[u * P] = u ? cmul(z[u], twL[u * a0]) : z[u];
-        }
-    __syncthreads();
-        // raw is free: start the next batch's samples
-        const int64_t bn = b + gridDim.x;
-        int offn = 0;
-        if (bn < nb) {
-            const int nfn = static_cast<int>((a.n_frames - bn * F) < F ? (a.n_frames - bn * F) : F);
-            offn = stage_async(a.frames, bn * F * static_cast<int64_t>(N), static_cast<int64_t>(nfn) * N, raw);
+                for (int bq = 0; bq < Q; ++bq) z[bq] = Yf[P * bq];
+                Dft<Q>::run(z);
+#pragma unroll
+                for (int u = 0; u < Q; ++u) Yf[u * P] = u ? cmul(z[u], twL[u * a0]) : z[u];
+            }
+            __syncthreads();
+        } else {
+            // ---------------- stage 1: fold, Q-point DFT, twiddle ----------------
+            for (int item = threadIdx.x; item < nf * P; item += blockDim.x) {
+                const int f = item / P;
+                const int a0 = item - f * P;
+                const int16_t* xs = raw + off + f * N + a0;
+                float2 z[Q];
+#pragma unroll
+                for (int bq = 0; bq < Q; ++bq) {
+                    const int16_t* xp = xs + P * bq;
+                    int D[MH];
+#pragma unroll
+                    for (int j = 0; j < MH; ++j) D[j] = static_cast<int>(xp[L * j]) + sg * static_cast<int>(xp[L * (j + MH)]);
+                    const int E1 = D[1] + sg * D[4], F1 = D[1] - sg * D[4];
+                    const int E2 = D[2] + sg * D[3], F2 = D[2] - sg * D[3];
+                    float2 fz;
+                    fz.x = fmaf(static_cast<float>(E2), c2, fmaf(static_cast<float>(E1), c1, static_cast<float>(D[0])));
+                    fz.y = fmaf(static_cast<float>(F2), s2, static_cast<float>(F1) * s1);
+                    z[bq] = cmul(fz, twN[a0 + P * bq]);
+                }
+                Dft<Q>::run(z);
+                float2* Yf = Yb + f * L + a0;
+#pragma unroll
+                for (int u = 0; u < Q; ++u) Yf[u * P] = u ? cmul(z[u], twL[u * a0]) : z[u];
+            }
+            __syncthreads();
+            // raw is free: start the next batch's samples
+            const int64_t bn = b + gridDim.x;
+            if (bn < nb) {
+                const int nfn = static_cast<int>((a.n_frames - bn * F) < F ? (a.n_frames - bn * F) : F);
+                offn = stage_async(a.frames, bn * F * static_cast<int64_t>(N), static_cast<int64_t>(nfn) * N, raw);
+            }
         }
         // ---------------- stage 2: P-point DFT over a, tooth magnitudes -------
         for (int item = threadIdx.x; item < nf * Q; item += blockDim.x) {
