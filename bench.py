@@ -132,6 +132,8 @@ GEOMETRIES = {
     "wide": ("WIDE", dict(snr_db=30.0, center_amp_hz=20e6)),
     "tiny": ("TINY", dict(sigma=0.01 * 2048, center_amp_hz=5e6)),
     "serve4096": ("SERVE_4096", dict(snr_db=30.0, center_amp_hz=20e6)),
+    # the paper's digitiser frame: 8-bit samples at 2.2 GS/s, 2200 per frame
+    "paper8": ("PAPER_8BIT", dict(snr_db=30.0, center_amp_hz=20e6, bits=8)),
 }
 
 
@@ -156,7 +158,7 @@ def build_workload(args, n_frames, n_ref, device, seed_offset=0):
         kw = dict(centers=lp["c"], fwhm_hz=lp["fwhm"], snr_db=lp["snr_db"])
         noise = dict(snr_db=30.0)
     else:
-        noise = {k: v for k, v in kw.items() if k in ("snr_db", "sigma")}
+        noise = {k: v for k, v in kw.items() if k in ("snr_db", "sigma", "bits")}
     fr = synth.frames(stream, n_frames, device=device, **kw)
     rf = synth.frames(stream, n_ref, cavity=False, noise_stream=1, device=device, **noise)
     return g, fr["frames"], rf["frames"]
@@ -185,7 +187,7 @@ def kernel_rooflines(stage_ms, stage_launches, n, g, T, args, mean_iters, hbm, b
         frames = n * args.steps_timed / cnt
         r = {"launches": cnt, "ms_per_launch": per * 1e3}
         if st == "readout" and args.readout in ("fft", "fold"):
-            b = (2 * g.frame_len + 4 * T) * frames
+            b = (args.sample_bytes * g.frame_len + 4 * T) * frames
             r.update(bound="hbm", achieved=b / per / 1e9, peak=hbm, unit="GB/s")
         elif st == "readout":
             f = 2.0 * g.frame_len * 2 * T * frames
@@ -254,8 +256,10 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     n = args.frames
     g, frames, ref_frames = build_workload(args, n, args.ref_frames, dev, seed_offset=rank)
+    args.sample_bytes = frames.element_size()
+    process = cg.cg_process_i8 if frames.dtype == torch.int8 else cg.cg_process
     plan0 = cg.Plan(g.sample_rate, g.frame_len, g.tooth_freqs, g.tooth_x)
-    ref = plan0.reference_accumulate(ref_frames)
+    ref = plan0.reference_accumulate(ref_frames.to(torch.int16))   # (8-bit samples widen exactly)
     plan0.close()
     del ref_frames
     plan = cg.Plan(g.sample_rate, g.frame_len, g.tooth_freqs, g.tooth_x, ref,
@@ -277,7 +281,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        cg.cg_process(plan.handle, frames, n, amps, None, params, rss, iters, status, stream)
+        process(plan.handle, frames, n, amps, None, params, rss, iters, status, stream)
 
     for _ in range(args.warmup):
         step()
@@ -313,7 +317,8 @@ def run_ours(args):
     mean_iters = float(iters.float().mean().item())
 
     hbm, bf16, peak_kind = _peaks()
-    bytes_per_frame = 2 * g.frame_len + 4 * T + 16 + 4 + 2 + 2
+    sb = args.sample_bytes
+    bytes_per_frame = sb * g.frame_len + 4 * T + 16 + 4 + 2 + 2
     kern = kernel_rooflines({k: v[0] for k, v in stages.items()}, {k: v[1] for k, v in stages.items()},
                             n, g, T, args, mean_iters, hbm, bf16)
     dominant = max(kern, key=lambda k: kern[k]["launches"] * kern[k]["ms_per_launch"])
@@ -325,16 +330,17 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic (seeded comb interferograms, 12-bit in int16)",
+        "dtype": "f32", "data": ("synthetic (seeded comb interferograms, 8-bit in int8)" if sb == 1 else
+                                 "synthetic (seeded comb interferograms, 12-bit in int16)"),
         "config": {"workload": workload_name(args, n),
                    "frames_per_gpu": n, "frame_len": g.frame_len, "teeth": T,
-                   "sample_rate_hz": g.sample_rate, "resident_bytes": 2 * g.frame_len * n,
-                   "l2": f"inputs ({2 * g.frame_len * n / 1e9:.1f} GB) larger than L2; no flush",
+                   "sample_rate_hz": g.sample_rate, "resident_bytes": sb * g.frame_len * n,
+                   "l2": f"inputs ({sb * g.frame_len * n / 1e9:.1f} GB) larger than L2; no flush",
                    "lanes_per_frame": plan.info["lanes_per_frame"],
                    "path": ["auto", "fused", "split", "pipeline"][plan.info["path"]],
                    "fft_len": plan.info["fft_len"], "readout": args.readout, "init": args.init,
                    "polish_iter": args.polish if args.init == "mlp" else None},
-        "input_gbs": total_frames * 2 * g.frame_len / (ms_step / 1e3) / 1e9,
+        "input_gbs": total_frames * sb * g.frame_len / (ms_step / 1e3) / 1e9,
         "roofline": {"kernel": dominant, "bound": dom.get("bound"), "achieved": dom.get("achieved"),
                      "peak": dom.get("peak"), "unit": dom.get("unit"), "frac": dom.get("frac"),
                      "traffic": dom.get("traffic"), "peak_kind": peak_kind},
@@ -368,14 +374,16 @@ def run_e2e(plan, frames_dev, n, T, dev, args, ws):
     import torch
     import paper_2307_12988_gb300 as cg
     N = plan.N
-    host_in = torch.empty((n, N), dtype=torch.int16, pin_memory=True)
+    sdt = frames_dev.dtype
+    process = cg.cg_process_i8 if sdt == torch.int8 else cg.cg_process
+    host_in = torch.empty((n, N), dtype=sdt, pin_memory=True)
     host_in.copy_(frames_dev.cpu())
     chunk = args.e2e_chunk
     nch = (n + chunk - 1) // chunk
     streams = [torch.cuda.Stream(dev) for _ in range(2)]
     bufs = []
     for _ in range(2):
-        bufs.append(dict(fr=torch.empty((chunk, N), dtype=torch.int16, device=dev),
+        bufs.append(dict(fr=torch.empty((chunk, N), dtype=sdt, device=dev),
                          amps=torch.empty((chunk, T), dtype=torch.float32, device=dev),
                          params=torch.empty((chunk, 4), dtype=torch.float32, device=dev),
                          rss=torch.empty(chunk, dtype=torch.float32, device=dev),
@@ -395,8 +403,8 @@ def run_e2e(plan, frames_dev, n, T, dev, args, ws):
             m = a1 - a0
             with torch.cuda.stream(s):
                 b["fr"][:m].copy_(host_in[a0:a1], non_blocking=True)
-                cg.cg_process(plan.handle, b["fr"], m, b["amps"], None, b["params"], b["rss"],
-                              b["iters"], b["status"], s)
+                process(plan.handle, b["fr"], m, b["amps"], None, b["params"], b["rss"],
+                        b["iters"], b["status"], s)
                 for k in ("amps", "params", "rss", "iters", "status"):
                     host_out[k][a0:a1].copy_(b[k][:m], non_blocking=True)
 
@@ -410,9 +418,10 @@ def run_e2e(plan, frames_dev, n, T, dev, args, ws):
     torch.cuda.synchronize()
     dt = max_over_ranks((time.perf_counter() - t0) / steps, dev)
     d2h = n * (4 * T + 16 + 4 + 2 + 2)
-    return {"value": weak_scaling_value(n, ws, dt), "unit": "spectra/s", "h2d_bytes_per_step": n * N * 2,
+    sb = frames_dev.element_size()
+    return {"value": weak_scaling_value(n, ws, dt), "unit": "spectra/s", "h2d_bytes_per_step": n * N * sb,
             "d2h_bytes_per_step": d2h, "chunk_frames": chunk, "steps": steps,
-            "input_gbs": n * ws * N * 2 / dt / 1e9}
+            "input_gbs": n * ws * N * sb / dt / 1e9}
 
 
 SERVE_STREAMS = [   # (geometry attribute, generator keywords): the three instruments of the serving workload

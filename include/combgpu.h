@@ -188,6 +188,22 @@ cg_status cg_readout(cg_plan_t plan, const int16_t* frames_dev, int64_t n_frames
                      float* amps_dev, float* y_dev, void* cuda_stream);
 
 /*
+ * cg_process_i8, cg_readout_i8 -- the same with 8-bit samples (int8, two's
+ * complement; the paper's digitiser format: "Experimental Setup", 8-bit at
+ * 2.2 GS/s).  frames_dev is int8 [n_frames][frame_len], any byte alignment.
+ * Supported where the pruned comb readout applies to an 8-bit frame of
+ * N = 2200 samples (every tooth bin at +-r mod 10, L = 220), with readout
+ * CG_READOUT_FFT; otherwise CG_ERR_UNSUPPORTED.  Results equal, bit for bit,
+ * those of cg_process / cg_readout on the same samples widened to int16.
+ * The path is always CG_PATH_PIPELINE.
+ */
+cg_status cg_process_i8(cg_plan_t plan, const int8_t* frames_dev, int64_t n_frames,
+                        float* amps_dev, float* y_dev, float* params_dev, float* rss_dev,
+                        int16_t* iters_dev, int16_t* status_dev, void* cuda_stream);
+cg_status cg_readout_i8(cg_plan_t plan, const int8_t* frames_dev, int64_t n_frames,
+                        float* amps_dev, float* y_dev, void* cuda_stream);
+
+/*
  * cg_fit -- only the initial guess and LM fit of cg_process, on normalised
  * spectra y_dev float [n][T].  p0_dev float [n][4] (abscissa units) or NULL
  * for the moment initial guess.  Outputs as in cg_process.

@@ -12,7 +12,8 @@ import numpy as np
 
 from . import _binding
 from ._binding import (CgError, cg_check_device, cg_fit, cg_opts_default, cg_plan, cg_plan_describe,
-                       cg_plan_destroy, cg_process, cg_readout, cg_reference_accumulate,
+                       cg_plan_destroy, cg_process, cg_process_i8, cg_readout, cg_readout_i8,
+                       cg_reference_accumulate,
                        cg_set_reference, cg_status_string, cg_version, load)
 from ._binding import (cg_mlp_adam, cg_mlp_backward, cg_mlp_create, cg_mlp_destroy, cg_mlp_forward,
                        cg_mlp_get_params, cg_mlp_infer, cg_mlp_load, cg_mlp_param_count, cg_mlp_save,
@@ -81,13 +82,14 @@ class Plan:
         return out
 
     def process(self, frames, want_y=True, stream=None):
-        """Whole path on int16 frames [n, N] resident on the device."""
+        """Whole path on int16 (or int8) frames [n, N] resident on the device."""
         n = frames.shape[0]
         if frames.dim() != 2 or frames.shape[1] != self.N:
             raise ValueError(f"frames must be [n, {self.N}]")
         o = self._outputs(n, frames.device, want_y)
-        cg_process(self.handle, frames, n, o["amps"], o["y"], o["params"], o["rss"],
-                   o["iters"], o["status"], stream)
+        import torch
+        fn = cg_process_i8 if frames.dtype == torch.int8 else cg_process
+        fn(self.handle, frames, n, o["amps"], o["y"], o["params"], o["rss"], o["iters"], o["status"], stream)
         return o
 
     def readout(self, frames, want_y=True, stream=None):
@@ -95,7 +97,8 @@ class Plan:
         n = frames.shape[0]
         amps = torch.empty((n, self.T), dtype=torch.float32, device=frames.device)
         y = torch.empty_like(amps) if want_y else None
-        cg_readout(self.handle, frames, n, amps, y, stream)
+        fn = cg_readout_i8 if frames.dtype == torch.int8 else cg_readout
+        fn(self.handle, frames, n, amps, y, stream)
         return amps, y
 
     def fit(self, y, p0=None, stream=None):

@@ -91,7 +91,9 @@ _SIGS = {
     "cg_plan_describe": (ctypes.c_int, [_P, ctypes.POINTER(cg_plan_info), _P]),
     "cg_set_reference": (ctypes.c_int, [_P, _P]),
     "cg_process": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P]),
+    "cg_process_i8": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P]),
     "cg_readout": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
+    "cg_readout_i8": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     "cg_fit": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
     "cg_reference_accumulate": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     "cg_reference_accumulate_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
@@ -246,6 +248,18 @@ def cg_process(plan: int, frames, n_frames: int, amps, y, params, rss, iters, st
     _check(load().cg_process(plan, _ptr(frames), int(n_frames), _ptr(amps), _ptr(y),
                              _ptr(params), _ptr(rss), _ptr(iters), _ptr(status),
                              _stream(stream)), "cg_process")
+
+
+def cg_process_i8(plan: int, frames, n_frames: int, amps, y, params, rss, iters, status,
+                  stream=None) -> None:
+    _check(load().cg_process_i8(plan, _ptr(frames), int(n_frames), _ptr(amps), _ptr(y),
+                                _ptr(params), _ptr(rss), _ptr(iters), _ptr(status),
+                                _stream(stream)), "cg_process_i8")
+
+
+def cg_readout_i8(plan: int, frames, n_frames: int, amps, y, stream=None) -> None:
+    _check(load().cg_readout_i8(plan, _ptr(frames), int(n_frames), _ptr(amps), _ptr(y),
+                                _stream(stream)), "cg_readout_i8")
 
 
 def cg_readout(plan: int, frames, n_frames: int, amps, y, stream=None) -> None:

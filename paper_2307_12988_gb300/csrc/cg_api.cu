@@ -161,33 +161,6 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
         tom[zidx[k]] = k;
     }
     if (!p->fit_ok) return cudaSuccess;
-    // batch size: minimise idle thread slots of the two transform stages
-    // (stage 1: 10 items per frame, cost ~ 50 Q; stage 2: Q items, cost ~ 200)
-    int bestF = 2;
-    double best = 1e30;
-    // (at most ~52 KiB of shared memory per block keeps four blocks per SM)
-    for (int F = 2; F <= 32; ++F) {
-        const int bytes = 2 * N * F + 32 + 8 * L * F + 4 * T * F;
-        if (bytes > 52 * 1024) break;
-        const double cost = (std::ceil(10.0 * F / 128.0) * 50.0 * Q + std::ceil(double(Q) * F / 128.0) * 200.0) / F;
-        if (cost < best - 1e-9) { best = cost; bestF = F; }
-    }
-    cg::FastArgs& a = p->fa;
-    a.N = N;
-    a.T = T;
-    a.F = bestF;
-    a.pair_isign = (p->r0 & 1) ? -1 : 1;
-    int off = 0;
-    a.sm_twL = off; off = align16(off + 8 * L);
-    a.sm_twN = off; off = align16(off + 8 * L);
-    a.sm_tom = off; off = align16(off + 4 * L);
-    a.sm_iref = off; off = align16(off + 4 * T);
-    a.sm_u = 0;
-    a.sm_raw = off; off = align16(off + 2 * N * bestF + 32);
-    a.sm_Y = off; off = align16(off + 8 * L * bestF);
-    a.sm_amps = off; off = align16(off + 4 * T * bestF);
-    a.sm_y = 0;
-    a.sm_total = off;
     std::vector<float2> tw5(5);
     for (int j = 0; j < 5; ++j) {
         const double ang = -kTwoPi * static_cast<double>((p->r0 * j) % 10) / 10.0;
@@ -196,20 +169,57 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
     cudaError_t e;
     if ((e = upload(&p->d.tw_M5, tw5)) != cudaSuccess) return e;
     if ((e = upload(&p->d.tooth_of_m, tom)) != cudaSuccess) return e;
-    a.twL = p->d.tw_L;
-    a.twN = p->d.tw_n1;
-    a.twM = p->d.tw_M5;
-    a.tooth_of_m = p->d.tooth_of_m;
-    a.inv_ref = p->d.inv_ref;
-    a.u = p->d.u;
-    void* fr = cg::fast_readout_ptr(Q);
-    if ((e = cg::raise_smem_limit(fr, a.sm_total)) != cudaSuccess) return e;
-    int occ = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fr, 128, a.sm_total)) != cudaSuccess) return e;
-    if (occ < 1) return cudaSuccess;
-    p->grid_fast = p->num_sms * occ;
+    // batch size and layout for samples of sb bytes: minimise idle thread
+    // slots of the two transform stages (stage 1: 10 items per frame, cost
+    // ~ 50 Q; stage 2: Q items, cost ~ 200); at most ~52 KiB of shared
+    // memory per block keeps four blocks per SM
+    auto layout = [&](int sb, cg::FastArgs& a, void* fn, int& grid) -> cudaError_t {
+        int bestF = 2;
+        double best = 1e30;
+        for (int F = 2; F <= 32; ++F) {
+            const int bytes = sb * N * F + 32 + 8 * L * F + 4 * T * F;
+            if (bytes > 52 * 1024) break;
+            const double cost =
+                (std::ceil(10.0 * F / 128.0) * 50.0 * Q + std::ceil(double(Q) * F / 128.0) * 200.0) / F;
+            if (cost < best - 1e-9) { best = cost; bestF = F; }
+        }
+        a.N = N;
+        a.T = T;
+        a.F = bestF;
+        a.pair_isign = (p->r0 & 1) ? -1 : 1;
+        int off = 0;
+        a.sm_twL = off; off = align16(off + 8 * L);
+        a.sm_twN = off; off = align16(off + 8 * L);
+        a.sm_tom = off; off = align16(off + 4 * L);
+        a.sm_iref = off; off = align16(off + 4 * T);
+        a.sm_u = 0;
+        a.sm_raw = off; off = align16(off + sb * N * bestF + 32);
+        a.sm_Y = off; off = align16(off + 8 * L * bestF);
+        a.sm_amps = off; off = align16(off + 4 * T * bestF);
+        a.sm_y = 0;
+        a.sm_total = off;
+        a.twL = p->d.tw_L;
+        a.twN = p->d.tw_n1;
+        a.twM = p->d.tw_M5;
+        a.tooth_of_m = p->d.tooth_of_m;
+        a.inv_ref = p->d.inv_ref;
+        a.u = p->d.u;
+        cudaError_t e2 = cg::raise_smem_limit(fn, a.sm_total);
+        if (e2 != cudaSuccess) return e2;
+        int occ = 0;
+        if ((e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 128, a.sm_total)) != cudaSuccess) return e2;
+        grid = p->num_sms * occ;
+        return cudaSuccess;
+    };
+    if ((e = layout(2, p->fa, cg::fast_readout_ptr(Q), p->grid_fast)) != cudaSuccess) return e;
+    if (p->grid_fast < 1) return cudaSuccess;
     p->Q = Q;
     p->fast_ok = true;
+    if (void* fr8 = cg::fast_readout_ptr(Q, 1)) {
+        // int8 samples: the staging takes half the bytes, so more frames per block
+        if ((e = layout(1, p->fa8, fr8, p->grid_fast8)) != cudaSuccess) return e;
+        p->fast_i8_ok = p->grid_fast8 >= 1;
+    }
     return cudaSuccess;
 }
 
@@ -676,11 +686,23 @@ static cg_status check_frames(const cg_plan_s* p, const int16_t* frames, int64_t
     return CG_OK;
 }
 
-cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps, float* y,
-                     float* params, float* rss, int16_t* iters, int16_t* status, void* stream)
+static cg_status check_frames_i8(const cg_plan_s* p, const int8_t* frames, int64_t n)
 {
-    cg_status st = check_frames(p, frames, n);
-    if (st != CG_OK) return st;
+    if (!p) return fail(CG_ERR_ARG, "plan is NULL");
+    if (n < 0) return fail(CG_ERR_ARG, "n_frames < 0");
+    if (n > 0 && !frames) return fail(CG_ERR_ARG, "frames_dev is NULL");
+    if (n > (int64_t(1) << 40) / p->N) return fail(CG_ERR_ARG, "n_frames too large");
+    if (!p->fast_i8_ok || p->opts.readout != CG_READOUT_FFT)
+        return fail(CG_ERR_UNSUPPORTED,
+                    "8-bit samples are read out by the pruned comb transform only (N = 2200 with every tooth "
+                    "bin at +-r mod 10, readout CG_READOUT_FFT)");
+    return CG_OK;
+}
+
+// The whole path for int16 (sbytes = 2) or int8 (sbytes = 1) frames.
+static cg_status process_impl(cg_plan_t p, const void* frames, int sbytes, int64_t n, float* amps, float* y,
+                              float* params, float* rss, int16_t* iters, int16_t* status, void* stream)
+{
     if (n == 0) return CG_OK;
     if (!amps || !params) return fail(CG_ERR_ARG, "amps_dev and params_dev are required");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -690,13 +712,14 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
     // both comb readouts read sample pairs as 32-bit words (frames 4-byte
     // aligned); otherwise the pipeline reads out with the general transform
     const bool aligned4 = !(reinterpret_cast<uintptr_t>(frames) & 3);
+    const int16_t* frames16 = static_cast<const int16_t*>(frames);   // the non-pipeline paths (int16 only)
     const bool fold = p->opts.readout == CG_READOUT_FOLD_GEMM && p->fold_ok && aligned4;
     if (mlp && !p->mlp_ok) return fail(CG_ERR_STATE, "init is CG_INIT_MLP but no network is loaded (cg_mlp_load)");
     int path = p->opts.path;
     if (path == CG_PATH_AUTO) path = p->fit_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED;
     if (path == CG_PATH_PIPELINE && !p->fit_ok) path = CG_PATH_FUSED;
     // tensor-core readouts or learned guess: readout, then guess and fit kernels
-    if (p->opts.readout != CG_READOUT_FFT || mlp) path = CG_PATH_PIPELINE;
+    if (p->opts.readout != CG_READOUT_FFT || mlp || sbytes == 1) path = CG_PATH_PIPELINE;
     const bool fast = !gemm && !fold && p->fast_ok && aligned4;
     const bool pow2 = !gemm && !fold && !fast && p->pow2_ok && aligned4;
     if (path == CG_PATH_PIPELINE) {
@@ -720,7 +743,8 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
         for (int64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += p->chunk) {
             const int64_t m = (n - c0) < p->chunk ? (n - c0) : p->chunk;
             const int64_t T = p->T;
-            const int16_t* fc = frames + c0 * p->N;
+            const char* fb = static_cast<const char*>(frames) + c0 * p->N * sbytes;
+            const int16_t* fc = reinterpret_cast<const int16_t*>(fb);
             float* ac = amps + c0 * T;
             float* yc = y ? y + c0 * T : nullptr;
             float* pc = params + c0 * 4;
@@ -728,6 +752,8 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
             int16_t* ic = iters ? iters + c0 : nullptr;
             int16_t* sc = status ? status + c0 : nullptr;
             e = timed(p, CG_STAGE_READOUT, p->s_read, [&] {
+                if (sbytes == 1)
+                    return cg::launch_fast_readout_i8(p, reinterpret_cast<const int8_t*>(fb), m, ac, yc, p->s_read);
                 return gemm   ? cg::launch_gemm_readout(p, fc, m, ac, yc, p->s_read)
                        : fold ? cg::launch_fold_readout(p, fc, m, ac, yc, p->s_read)
                        : fast ? cg::launch_fast_readout(p, fc, m, ac, yc, p->s_read)
@@ -778,15 +804,42 @@ cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps,
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join_f, 0);
     } else if (path == CG_PATH_FUSED) {
         e = timed(p, CG_STAGE_FUSED, s,
-                  [&] { return cg::launch_fused(p, frames, n, amps, y, params, rss, iters, status, s); });
+                  [&] { return cg::launch_fused(p, frames16, n, amps, y, params, rss, iters, status, s); });
     } else {
-        e = timed(p, CG_STAGE_READOUT, s, [&] { return cg::launch_readout(p, frames, n, amps, y, s); });
+        e = timed(p, CG_STAGE_READOUT, s, [&] { return cg::launch_readout(p, frames16, n, amps, y, s); });
         // without y_dev the fit reads the magnitudes and applies the reference itself
         if (e == cudaSuccess)
             e = timed(p, CG_STAGE_FIT, s,
                       [&] { return cg::launch_fit(p, y, amps, n, nullptr, params, rss, iters, status, s); });
     }
     if (e != cudaSuccess) return cuda_fail(e, "cg_process launch");
+    return CG_OK;
+}
+
+cg_status cg_process(cg_plan_t p, const int16_t* frames, int64_t n, float* amps, float* y,
+                     float* params, float* rss, int16_t* iters, int16_t* status, void* stream)
+{
+    cg_status st = check_frames(p, frames, n);
+    if (st != CG_OK) return st;
+    return process_impl(p, frames, 2, n, amps, y, params, rss, iters, status, stream);
+}
+
+cg_status cg_process_i8(cg_plan_t p, const int8_t* frames, int64_t n, float* amps, float* y,
+                        float* params, float* rss, int16_t* iters, int16_t* status, void* stream)
+{
+    cg_status st = check_frames_i8(p, frames, n);
+    if (st != CG_OK) return st;
+    return process_impl(p, frames, 1, n, amps, y, params, rss, iters, status, stream);
+}
+
+cg_status cg_readout_i8(cg_plan_t p, const int8_t* frames, int64_t n, float* amps, float* y, void* stream)
+{
+    cg_status st = check_frames_i8(p, frames, n);
+    if (st != CG_OK) return st;
+    if (n == 0) return CG_OK;
+    if (!amps && !y) return fail(CG_ERR_ARG, "amps_dev and y_dev are both NULL");
+    const cudaError_t e = cg::launch_fast_readout_i8(p, frames, n, amps, y, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cg_readout_i8 launch");
     return CG_OK;
 }
 

@@ -31,7 +31,7 @@
 
 namespace cg {
 
-template <int P, int Q>
+template <int P, int Q, class S>
 __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
 {
     constexpr int L = P * Q;
@@ -44,7 +44,8 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
     float2* twN = reinterpret_cast<float2*>(sm + a.sm_twN);
     int* tom = reinterpret_cast<int*>(sm + a.sm_tom);
     float* iref = reinterpret_cast<float*>(sm + a.sm_iref);
-    int16_t* raw = reinterpret_cast<int16_t*>(sm + a.sm_raw);
+    S* raw = reinterpret_cast<S*>(sm + a.sm_raw);
+    const S* frames = static_cast<const S*>(a.frames);
     float2* Yb = reinterpret_cast<float2*>(sm + a.sm_Y);
     float* amp_s = reinterpret_cast<float*>(sm + a.sm_amps);
     const int T = a.T, N = a.N, F = a.F;
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
     int off = 0;
     if (b < nb) {
         const int nf0 = static_cast<int>((a.n_frames - b * F) < F ? (a.n_frames - b * F) : F);
-        off = stage_async(a.frames, b * F * static_cast<int64_t>(N), static_cast<int64_t>(nf0) * N, raw);
+        off = stage_async(frames, b * F * static_cast<int64_t>(N), static_cast<int64_t>(nf0) * N, raw);
     }
     for (; b < nb; b += gridDim.x) {
         const int64_t f0 = b * F;
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
             for (int item = threadIdx.x; item < nf * L; item += blockDim.x) {
                 const int f = item / L;
                 const int m = item - f * L;
-                const int16_t* xp = raw + off + f * N + m;
+                const S* xp = raw + off + f * N + m;
                 int D[MH];
 #pragma unroll
                 for (int j = 0; j < MH; ++j) D[j] = static_cast<int>(xp[L * j]) + sg * static_cast<int>(xp[L * (j + MH)]);
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
             const int64_t bn = b + gridDim.x;
             if (bn < nb) {
                 const int nfn = static_cast<int>((a.n_frames - bn * F) < F ? (a.n_frames - bn * F) : F);
-                offn = stage_async(a.frames, bn * F * static_cast<int64_t>(N), static_cast<int64_t>(nfn) * N, raw);
+                offn = stage_async(frames, bn * F * static_cast<int64_t>(N), static_cast<int64_t>(nfn) * N, raw);
             }
             // ---------------- stage 1: Q-point DFT over b, twiddle (in place) --
             for (int item = threadIdx.x; item < nf * P; item += blockDim.x) {
@@ -114,11 +115,11 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
             for (int item = threadIdx.x; item < nf * P; item += blockDim.x) {
                 const int f = item / P;
                 const int a0 = item - f * P;
-                const int16_t* xs = raw + off + f * N + a0;
+                const S* xs = raw + off + f * N + a0;
                 float2 z[Q];
 #pragma unroll
                 for (int bq = 0; bq < Q; ++bq) {
-                    const int16_t* xp = xs + P * bq;
+                    const S* xp = xs + P * bq;
                     int D[MH];
 #pragma unroll
                     for (int j = 0; j < MH; ++j) D[j] = static_cast<int>(xp[L * j]) + sg * static_cast<int>(xp[L * (j + MH)]);
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
             const int64_t bn = b + gridDim.x;
             if (bn < nb) {
                 const int nfn = static_cast<int>((a.n_frames - bn * F) < F ? (a.n_frames - bn * F) : F);
-                offn = stage_async(a.frames, bn * F * static_cast<int64_t>(N), static_cast<int64_t>(nfn) * N, raw);
+                offn = stage_async(frames, bn * F * static_cast<int64_t>(N), static_cast<int64_t>(nfn) * N, raw);
             }
         }
         // ---------------- stage 2: P-point DFT over a, tooth magnitudes -------
@@ -687,16 +688,19 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-template <int P, int Q>
-static void* fast_fn() { return reinterpret_cast<void*>(&fast_readout_kernel<P, Q>); }
+template <int P, int Q, class S>
+static void* fast_fn() { return reinterpret_cast<void*>(&fast_readout_kernel<P, Q, S>); }
 
-void* fast_readout_ptr(int Q)
+// the instantiated coset readouts: L = 10 Q with Q in {10, 11, 22, 25};
+// int16 samples, and int8 samples for the 8-bit 2200-sample frame (Q = 22)
+void* fast_readout_ptr(int Q, int sample_bytes)
 {
+    if (sample_bytes == 1) return Q == 22 ? fast_fn<10, 22, int8_t>() : nullptr;
     switch (Q) {
-    case 10: return fast_fn<10, 10>();
-    case 11: return fast_fn<10, 11>();
-    case 22: return fast_fn<10, 22>();
-    case 25: return fast_fn<10, 25>();
+    case 10: return fast_fn<10, 10, int16_t>();
+    case 11: return fast_fn<10, 11, int16_t>();
+    case 22: return fast_fn<10, 22, int16_t>();
+    case 25: return fast_fn<10, 25, int16_t>();
     default: return nullptr;
     }
 }
@@ -780,18 +784,31 @@ int init_npad(int n_outer)
     return 0;
 }
 
-cudaError_t launch_fast_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps,
-                                float* y, cudaStream_t s)
+static cudaError_t launch_fast(const cg_plan_s* p, const void* frames, int sample_bytes, int64_t n, float* amps,
+                               float* y, cudaStream_t s)
 {
-    FastArgs a = p->fa;
+    FastArgs a = sample_bytes == 1 ? p->fa8 : p->fa;
     a.frames = frames;
     a.n_frames = n;
     a.amps = amps;
     a.y = y;
     const int64_t nb = (n + a.F - 1) / a.F;
-    const int grid = static_cast<int>(nb < p->grid_fast ? nb : p->grid_fast);
+    const int gmax = sample_bytes == 1 ? p->grid_fast8 : p->grid_fast;
+    const int grid = static_cast<int>(nb < gmax ? nb : gmax);
     void* args[] = {&a};
-    return cudaLaunchKernel(fast_readout_ptr(p->Q), dim3(grid), dim3(128), args, a.sm_total, s);
+    return cudaLaunchKernel(fast_readout_ptr(p->Q, sample_bytes), dim3(grid), dim3(128), args, a.sm_total, s);
+}
+
+cudaError_t launch_fast_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps,
+                                float* y, cudaStream_t s)
+{
+    return launch_fast(p, frames, 2, n, amps, y, s);
+}
+
+cudaError_t launch_fast_readout_i8(const cg_plan_s* p, const int8_t* frames, int64_t n, float* amps, float* y,
+                                   cudaStream_t s)
+{
+    return launch_fast(p, frames, 1, n, amps, y, s);
 }
 
 cudaError_t launch_init(const cg_plan_s* p, const float* y, const float* amps, int64_t n,

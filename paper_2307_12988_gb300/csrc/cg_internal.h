@@ -45,7 +45,7 @@ struct ReadoutArgs {
 
 // Arguments of the fast readout (comb geometries, N = 10 P Q).
 struct FastArgs {
-    const int16_t* frames;
+    const void* frames;      // int16 or int8 samples (the kernel's instantiation)
     int64_t n_frames;
     int N, T, F;
     int pair_isign;          // (-1)^r: sign pairing x_j with x_{j+5} in the fold
@@ -221,6 +221,9 @@ struct cg_plan_s {
     // throughput path (fast readout + register-resident LM over chunks)
     bool fit_ok = false;     // init + fit kernels of the throughput path configured
     bool fast_ok = false;    // geometry admits the fast readout
+    bool fast_i8_ok = false; // ... and an int8 instantiation exists for it
+    cg::FastArgs fa8{};      // its batch size and layout
+    int grid_fast8 = 0;
     // split-precision GEMM readout
     CUtensorMap gemm_map{};
     int gemm_split_x = 1, gemm_smem = 0, gemm_ntiles = 0;
@@ -283,7 +286,7 @@ cudaError_t launch_reference_into(const cg_plan_s* p, const int16_t* frames, int
 FitArgs make_fit_args(const cg_plan_s* p);
 
 // throughput path (cg_fast.cu)
-void* fast_readout_ptr(int Q);
+void* fast_readout_ptr(int Q, int sample_bytes = 2);
 void* init_ptr(int npad);
 int init_npad(int n_outer);
 void* fit2_ptr(int G, int PPL, bool exact);
@@ -291,6 +294,8 @@ int fit2_ppl(int G, int T, bool* exact);
 int fit2_threads(int G);
 void* fit1_ptr();   // lane-per-frame LM kernel (cg_fit1.cu)
 size_t fit2_smem(int G, int T);
+cudaError_t launch_fast_readout_i8(const cg_plan_s* p, const int8_t* frames, int64_t n, float* amps, float* y,
+                                   cudaStream_t s);
 cudaError_t launch_fast_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps,
                                 float* y, cudaStream_t s);
 // options of a fit launch beyond the plan's: polish cap, frame list, fallback list

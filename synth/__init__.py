@@ -75,6 +75,8 @@ TINY = Geometry(1.0e9, 1000, -10, 10)
 PAPER_RATE = Geometry(1.1e9, 1100, -49, 49)
 WIDE = Geometry(2.5e9, 2500, -110, 110)
 SERVE_4096 = Geometry(2.0e9, 4096, -100, 100)
+# the paper's digitiser frame: 8-bit samples at 2.2 GS/s, 2200 per 1 us row
+PAPER_8BIT = Geometry(2.2e9, 2200, -49, 49)
 
 
 @dataclasses.dataclass
@@ -122,19 +124,26 @@ def lineshape(x: np.ndarray, c: np.ndarray, fwhm: np.ndarray | float,
 def frames(stream: Stream, n_frames: int, *, first_frame: int = 0, cavity: bool = True,
            center_amp_hz: float = 5e6, drive_hz: float = DRIVE_HZ, fwhm_hz=FWHM_HZ,
            depth: float = 0.7, shape: str = "dip", sigma=None,
-           snr_db=None, noise_stream: int = 0, centers=None, device=None) -> dict:
+           snr_db=None, noise_stream: int = 0, centers=None, device=None, bits: int = 12) -> dict:
     """Synthesise ``n_frames`` int16 frames [n_frames, N] (see the module recipe).
 
     ``centers`` (per frame, Hz) replaces the sinusoidal drive; ``fwhm_hz``,
     ``sigma`` and ``snr_db`` may be per-frame arrays.  ``device`` = None / "cpu"
     uses numpy; a torch CUDA device builds the frames there with torch (for the
-    largest workloads).  Returns dict(frames, centers)."""
+    largest workloads).  ``bits`` = 12 (int16 storage) or 8 (int8, the paper's
+    digitiser format): full scale 2^(bits-1), the noise-free RMS a quarter of
+    it, the SNR-derived noise scaled with it (an explicit ``sigma`` is in
+    output units).  Returns dict(frames, centers)."""
     g = stream.geom
     N, T, fs = g.frame_len, g.n_teeth, g.sample_rate
+    if bits not in (8, 12):
+        raise ValueError("bits must be 8 or 12")
+    fs_full = 2.0 ** (bits - 1)
+    rms = RMS_TARGET * fs_full / FULL_SCALE
     if sigma is None:
-        sigma = 0.0 if snr_db is None else RMS_TARGET / 10.0 ** (np.asarray(snr_db, dtype=np.float64) / 20.0)
+        sigma = 0.0 if snr_db is None else rms / 10.0 ** (np.asarray(snr_db, dtype=np.float64) / 20.0)
     sigma = np.asarray(sigma, dtype=np.float64)
-    E = RMS_TARGET * math.sqrt(2.0 / T)
+    E = rms * math.sqrt(2.0 / T)
     idx = np.arange(first_frame, first_frame + n_frames, dtype=np.int64)
     t0 = idx.astype(np.float64) * N / fs
     if centers is None:
@@ -151,16 +160,16 @@ def frames(stream: Stream, n_frames: int, *, first_frame: int = 0, cavity: bool 
     ac, asn = amp * np.cos(psi), amp * np.sin(psi)
     if device is not None and str(device) != "cpu":
         out = _frames_torch(ac, asn, Cb, Sb, sigma, stream.seed, noise_stream,
-                            first_frame, device)
+                            first_frame, device, fs_full)
     else:
-        out = np.empty((n_frames, N), dtype=np.int16)
+        out = np.empty((n_frames, N), dtype=np.int8 if bits == 8 else np.int16)
         for s in range(0, n_frames, CHUNK):
             e = min(n_frames, s + CHUNK)
             sig = ac[s:e] @ Cb - asn[s:e] @ Sb
             if np.any(sigma > 0):
                 sg = sigma[s:e, None] if sigma.ndim else sigma
                 sig += sg * _chunk_noise(stream.seed, noise_stream, first_frame + s, e - s, N)
-            out[s:e] = np.clip(np.rint(sig), -FULL_SCALE, FULL_SCALE - 1).astype(np.int16)
+            out[s:e] = np.clip(np.rint(sig), -fs_full, fs_full - 1).astype(out.dtype)
     return dict(frames=out, centers=centers)
 
 
@@ -180,14 +189,15 @@ def _chunk_noise(seed: int, noise_stream: int, first: int, n: int, N: int) -> np
     return out
 
 
-def _frames_torch(ac, asn, Cb, Sb, sigma, seed, noise_stream, first_frame, device):
+def _frames_torch(ac, asn, Cb, Sb, sigma, seed, noise_stream, first_frame, device, fs_full=FULL_SCALE):
     import torch
     dev = torch.device(device)
     n = ac.shape[0]
     N = Cb.shape[1]
     Ct = torch.from_numpy(Cb.astype(np.float32)).to(dev)
     St = torch.from_numpy(Sb.astype(np.float32)).to(dev)
-    out = torch.empty((n, N), dtype=torch.int16, device=dev)
+    odt = torch.int8 if fs_full == 128.0 else torch.int16
+    out = torch.empty((n, N), dtype=odt, device=dev)
     gen = torch.Generator(device=dev)
     gen.manual_seed((seed * 1_000_003 + noise_stream * 7919 + first_frame) % (2**63))
     step = 1 << 16
@@ -200,7 +210,7 @@ def _frames_torch(ac, asn, Cb, Sb, sigma, seed, noise_stream, first_frame, devic
             sg = (torch.from_numpy(sigma[s:e].astype(np.float32)).to(dev)[:, None] if sigma.ndim
                   else float(sigma))
             sig += sg * torch.randn(sig.shape, generator=gen, device=dev)
-        out[s:e] = torch.clamp(torch.round(sig), -FULL_SCALE, FULL_SCALE - 1).to(torch.int16)
+        out[s:e] = torch.clamp(torch.round(sig), -fs_full, fs_full - 1).to(odt)
     return out
 
 

@@ -20,6 +20,8 @@ SPECS = {
     "paper_rate": (synth.PAPER_RATE, 1500, 1000, dict(snr_db=30.0, center_amp_hz=20e6)),
     "wide": (synth.WIDE, 400, 400, dict(snr_db=30.0, center_amp_hz=20e6)),
     "serve4096": (synth.SERVE_4096, 200, 300, dict(snr_db=30.0, center_amp_hz=20e6)),
+    # 8-bit samples at 2.2 GS/s, 2200-sample frames (the paper's digitiser)
+    "paper8": (synth.PAPER_8BIT, 1500, 1000, dict(snr_db=30.0, center_amp_hz=20e6, bits=8)),
     # the other power-of-two frame lengths of the full-transform readout
     "pow2_2048": (synth.Geometry(1.0e9, 2048, -40, 40), 300, 300, dict(snr_db=30.0, center_amp_hz=20e6)),
     "pow2_8192": (synth.Geometry(4.0e9, 8192, -100, 100), 150, 200, dict(snr_db=30.0, center_amp_hz=20e6)),
@@ -32,7 +34,7 @@ def workload(name: str) -> dict:
     seed = synth.BASE_SEED + sorted(SPECS).index(name)
     stream = synth.make_stream(geom, seed)
     fr = synth.frames(stream, n, **kw)
-    ref_kw = {k: v for k, v in kw.items() if k in ("sigma", "snr_db")}
+    ref_kw = {k: v for k, v in kw.items() if k in ("sigma", "snr_db", "bits")}
     rf = synth.frames(stream, n_ref, cavity=False, noise_stream=1, **ref_kw)
     bins = oracle.tooth_bins(geom.sample_rate, geom.frame_len, geom.tooth_freqs)
     ref = oracle.reference(rf["frames"], bins)
