@@ -3,7 +3,7 @@ benchmark times (GPU).
 
 Each case builds the benchmark's seeded workload on the device (10^6
 paper-rate frames; 4 x 10^5 wide frames for the split-precision GEMM readout;
-10^6 learned-guess frames), runs one ``cg_process`` call over all of it with
+10^6 learned-guess frames; 10^6 8-bit 2200-sample frames), runs one ``cg_process`` call over all of it with
 the benchmark's outputs (amplitudes, no y), then checks sampled frames one by
 one against the FP64 oracle (tooth amplitudes within 1e-5 of the reference,
 converged centres within 1e-4 of the linewidth) and properties that hold at
@@ -37,6 +37,7 @@ CASES = {
     "wide_gemm": (synth.WIDE, 400_000, dict(snr_db=30.0, center_amp_hz=20e6),
                   dict(readout=cg.READOUT_GEMM_SPLIT, sample_bits=12)),
     "learned_mlp": (synth.WIDE, 1_000_000, "learned", dict(init=cg.INIT_MLP)),
+    "paper8_int8": (synth.PAPER_8BIT, 1_000_000, dict(snr_db=30.0, center_amp_hz=20e6, bits=8), {}),
 }
 
 
@@ -65,7 +66,7 @@ def test_full_size_sampled_parity(dev, case):
         fwhm = lp["fwhm"]
         noise = dict(snr_db=30.0)
     else:
-        noise = {k: v for k, v in kw.items() if k in ("snr_db", "sigma")}
+        noise = {k: v for k, v in kw.items() if k in ("snr_db", "sigma", "bits")}
     frames = synth.frames(stream, n, device=dev, **kw)["frames"]
     ref_frames = synth.frames(stream, 2000, cavity=False, noise_stream=1, **noise)["frames"]
     bins = oracle.tooth_bins(g.sample_rate, g.frame_len, g.tooth_freqs)
@@ -80,7 +81,8 @@ def test_full_size_sampled_parity(dev, case):
         rss = torch.empty(n, dtype=torch.float32, device=dev)
         iters = torch.empty(n, dtype=torch.int16, device=dev)
         status = torch.empty(n, dtype=torch.int16, device=dev)
-        cg.cg_process(p.handle, frames, n, amps, None, params, rss, iters, status, None)
+        process = cg.cg_process_i8 if frames.dtype == torch.int8 else cg.cg_process
+        process(p.handle, frames, n, amps, None, params, rss, iters, status, None)
         torch.cuda.synchronize()
         cg.cg_check_device(p.handle)
         max_iter = 20
