@@ -69,6 +69,12 @@ def _load():
         "or_fit_batch": (None, [P, i64, P, i32, P, i32, f64, f64, P, P, P, P, P]),
         "or_process": (i32, [P, i64, i32, i32, P, P, P, i32, f64, f64, P, P, P, P, P, P]),
         "or_grid_fit": (None, [P, P, i32, P, i32, P, i32, P, P]),
+        "or_fano_model": (None, [P, i32, f64, f64, P, P]),
+        "or_fano_jacobian": (None, [P, i32, f64, f64, P, P]),
+        "or_fano_init": (None, [P, P, i32, f64, f64, f64, f64, P]),
+        "or_fano_fit_batch": (None, [P, i64, P, i32, f64, f64, f64, f64, f64, P, i32, f64, f64,
+                                     P, P, P, P, P]),
+        "or_fano_grid_fit": (None, [P, P, i32, f64, f64, P, i32, P, i32, P, i32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -241,4 +247,65 @@ def grid_fit(y, x, cgrid, ggrid):
     chi2 = ctypes.c_double()
     _load().or_grid_fit(_p(ya), _p(xa), xa.size, _p(cg), cg.size, _p(gg), gg.size,
                         _p(p), ctypes.byref(chi2))
+    return p, chi2.value
+
+
+# ---------------------------------------------------------------------------
+# The paper's Fano lineshape with box-constrained scale and offset (f1)
+# ---------------------------------------------------------------------------
+def fano_model(x, q, gamma, p) -> np.ndarray:
+    """m(x) = B + A (q + e)^2 / (1 + e^2), e = (x - c) / gamma, p = (c, A, B)."""
+    xa, pa = _f64(x), _f64(p)
+    out = np.empty(xa.size)
+    _load().or_fano_model(_p(xa), xa.size, float(q), float(gamma), _p(pa), _p(out))
+    return out
+
+
+def fano_jacobian(x, q, gamma, p) -> np.ndarray:
+    """d m / d (c, A, B) at each abscissa, shape [T, 3]."""
+    xa, pa = _f64(x), _f64(p)
+    out = np.empty((xa.size, 3))
+    _load().or_fano_jacobian(_p(xa), xa.size, float(q), float(gamma), _p(pa), _p(out))
+    return out
+
+
+def fano_init(y, x, q, gamma, A_bar, B_bar) -> np.ndarray:
+    ya, xa = _f64(y), _f64(x)
+    out = np.empty(3)
+    _load().or_fano_init(_p(ya), _p(xa), xa.size, float(q), float(gamma), float(A_bar), float(B_bar), _p(out))
+    return out
+
+
+def fano_fit_batch(y, x, q, gamma, A_bar, B_bar, box=0.1, p0=None, max_iter=20, tol=1e-6, lambda0=1e-3,
+                   converged=False):
+    """Box-constrained LM fit of each row of y[n, T] with the Fano model:
+    c free, A in A_bar (1 +- box), B in B_bar (1 +- box), q and gamma fixed.
+    Returns dict(init, params [n, 3] = (c, A, B), rss, iters, status)."""
+    ya = _f64(y)
+    if ya.ndim == 1:
+        ya = ya[None, :]
+    n, T = ya.shape
+    xa = _f64(x)
+    if converged:
+        max_iter, tol = CONVERGED_MAX_ITER, CONVERGED_TOL
+    pa = None if p0 is None else _f64(p0).reshape(n, 3)
+    init = np.empty((n, 3))
+    params = np.empty((n, 3))
+    rss = np.empty(n)
+    iters = np.empty(n, dtype=np.int32)
+    status = np.empty(n, dtype=np.int32)
+    _load().or_fano_fit_batch(_p(ya), n, _p(xa), T, float(q), float(gamma), float(A_bar), float(B_bar),
+                              float(box), _p(pa), int(max_iter), float(tol), float(lambda0), _p(init),
+                              _p(params), _p(rss), _p(iters), _p(status))
+    return dict(init=init, params=params, rss=rss, iters=iters, status=status)
+
+
+def fano_grid_fit(y, x, q, gamma, cgrid, Agrid, Bgrid):
+    """Brute force: least chi^2 over the (c, A, B) grid; returns (p, chi2)."""
+    ya, xa = _f64(y), _f64(x)
+    cg_, ag, bg = _f64(cgrid), _f64(Agrid), _f64(Bgrid)
+    p = np.empty(3)
+    chi2 = ctypes.c_double()
+    _load().or_fano_grid_fit(_p(ya), _p(xa), xa.size, float(q), float(gamma), _p(cg_), cg_.size, _p(ag), ag.size,
+                             _p(bg), bg.size, _p(p), ctypes.byref(chi2))
     return p, chi2.value

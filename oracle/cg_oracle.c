@@ -34,6 +34,10 @@
  *     median of the outer fifth of the teeth (the paper's own initial guess,
  *     a 7x7 median filter over the time x tooth image, is not implemented).
  *
+ * The paper's own lineshape (a Fano profile with the centre free, scale and
+ * offset boxed to +-10 % of averages, asymmetry and width fixed) is the
+ * second model here (or_fano_*), a box-constrained LM over (c, A, B).
+ *
  * Parity: the DFT is pinned by closed forms (pure tone gives a N/2,
  * X_0 = sum x, X_{N/2} = alternating sum, Parseval) and by numpy's rfft;
  * the LM optimum by noise-free recovery, shift/scale/mirror invariants,
@@ -496,5 +500,225 @@ void or_grid_fit(const double* y, const double* x, int T,
             }
         }
     }
+    *chi2_best = best;
+}
+
+/* ------------------------------------------------------------------ */
+/* The paper's fitted lineshape: a Fano profile        */
+/* ("Data Capture and Processing", fit paragraph; Fano 1961)           */
+/*   eps = (x - c) / gamma,   F = (q + eps)^2 / (1 + eps^2),           */
+/*   m(x) = B + A F                                                    */
+/* with the centre c free, the scale A and offset B held to a box      */
+/* [lo, hi] of +-box around pre-computed averages (A_bar, B_bar), and  */
+/* the asymmetry q and width gamma fixed.  Bounds are applied by       */
+/* clamping A and B after every trial step (the constraint handling    */
+/* of the LM library the paper uses).  q = 0 gives the Lorentzian dip   */
+/* B + A - A / (1 + eps^2).                                            */
+/*   dm/dc = -A F'(eps) / gamma,  F'(eps) = 2 (q+eps)(1 - q eps)/(1+eps^2)^2 */
+/*   dm/dA = F,                    dm/dB = 1                            */
+/* ------------------------------------------------------------------ */
+void or_fano_model(const double* x, int T, double q, double gamma, const double* p, double* m)
+{
+    for (int k = 0; k < T; ++k) {
+        const double e = (x[k] - p[0]) / gamma;
+        m[k] = p[2] + p[1] * (q + e) * (q + e) / (1.0 + e * e);
+    }
+}
+
+/* Jacobian rows (dm/dc, dm/dA, dm/dB), p = (c, A, B) */
+void or_fano_jacobian(const double* x, int T, double q, double gamma, const double* p, double* J)
+{
+    for (int k = 0; k < T; ++k) {
+        const double e = (x[k] - p[0]) / gamma;
+        const double d = 1.0 + e * e;
+        J[3 * k + 0] = -p[1] * 2.0 * (q + e) * (1.0 - q * e) / (d * d) / gamma;
+        J[3 * k + 1] = (q + e) * (q + e) / d;
+        J[3 * k + 2] = 1.0;
+    }
+}
+
+static double fano_eval(const double* x, const double* y, int T, double q, double gamma, const double* p,
+                        double H[3][3], double grad[3])
+{
+    double chi2 = 0.0;
+    double J[3];
+    for (int i = 0; i < 3; ++i) {
+        grad[i] = 0.0;
+        for (int j = 0; j < 3; ++j) H[i][j] = 0.0;
+    }
+    for (int k = 0; k < T; ++k) {
+        const double e = (x[k] - p[0]) / gamma;
+        const double d = 1.0 + e * e;
+        const double F = (q + e) * (q + e) / d;
+        const double r = y[k] - (p[2] + p[1] * F);
+        J[0] = -p[1] * 2.0 * (q + e) * (1.0 - q * e) / (d * d) / gamma;
+        J[1] = F;
+        J[2] = 1.0;
+        chi2 += r * r;
+        for (int i = 0; i < 3; ++i) {
+            grad[i] += J[i] * r;
+            for (int j = 0; j < 3; ++j) H[i][j] += J[i] * J[j];
+        }
+    }
+    return chi2;
+}
+
+/* (H + lambda diag H) delta = grad for 3 parameters, Jacobi-scaled Cholesky */
+static int fano_solve(const double H[3][3], double lambda, const double grad[3], double delta[3])
+{
+    double s[3], M[3][3], Lc[3][3], z[3], u[3];
+    for (int i = 0; i < 3; ++i) {
+        if (!(H[i][i] > 0.0) || !isfinite(H[i][i])) return -1;
+        s[i] = 1.0 / sqrt(H[i][i]);
+    }
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) M[i][j] = H[i][j] * s[i] * s[j];
+        M[i][i] = 1.0 + lambda;
+    }
+    memset(Lc, 0, sizeof(Lc));
+    for (int j = 0; j < 3; ++j) {
+        double v = M[j][j];
+        for (int t = 0; t < j; ++t) v -= Lc[j][t] * Lc[j][t];
+        if (!(v > 0.0)) return -1;
+        Lc[j][j] = sqrt(v);
+        for (int i = j + 1; i < 3; ++i) {
+            double w = M[i][j];
+            for (int t = 0; t < j; ++t) w -= Lc[i][t] * Lc[j][t];
+            Lc[i][j] = w / Lc[j][j];
+        }
+    }
+    for (int i = 0; i < 3; ++i) {
+        double v = grad[i] * s[i];
+        for (int t = 0; t < i; ++t) v -= Lc[i][t] * z[t];
+        z[i] = v / Lc[i][i];
+    }
+    for (int i = 2; i >= 0; --i) {
+        double v = z[i];
+        for (int t = i + 1; t < 3; ++t) v -= Lc[t][i] * u[t];
+        u[i] = v / Lc[i][i];
+    }
+    for (int i = 0; i < 3; ++i) delta[i] = u[i] * s[i];
+    return 0;
+}
+
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Box of +-box around avg (ordered whatever the sign of avg). */
+static void fano_box(double avg, double box, double* lo, double* hi)
+{
+    const double a = avg * (1.0 - box), b = avg * (1.0 + box);
+    *lo = a < b ? a : b;
+    *hi = a < b ? b : a;
+}
+
+/* Initial guess: the centre at the lowest tooth (the paper's "lowest value"
+ * reading) moved to where the profile's minimum lies, eps = -q, i.e.
+ * c0 = x_min + q gamma; A and B at their averages. */
+void or_fano_init(const double* y, const double* x, int T, double q, double gamma, double A_bar, double B_bar,
+                  double* p0)
+{
+    int kmin = 0;
+    for (int k = 1; k < T; ++k)
+        if (y[k] < y[kmin]) kmin = k;
+    p0[0] = x[kmin] + q * gamma;
+    p0[1] = A_bar;
+    p0[2] = B_bar;
+}
+
+/* Box-constrained Levenberg-Marquardt of one spectrum, p = (c, A, B):
+ * trial = clamp(p + delta) onto the box; accept / reject, lambda and the
+ * stopping rule as in or_lm_fit. */
+void or_fano_fit(const double* y, const double* x, int T, double q, double gamma, double A_bar, double B_bar,
+                 double box, const double* p0, int max_iter, double tol, double lambda0, double* p_out,
+                 double* rss, int* iters, int* status)
+{
+    double Alo, Ahi, Blo, Bhi;
+    fano_box(A_bar, box, &Alo, &Ahi);
+    fano_box(B_bar, box, &Blo, &Bhi);
+    double p[3], H[3][3], grad[3];
+    p[0] = p0[0];
+    p[1] = clampd(p0[1], Alo, Ahi);
+    p[2] = clampd(p0[2], Blo, Bhi);
+    double lambda = lambda0;
+    double chi2 = fano_eval(x, y, T, q, gamma, p, H, grad);
+    int it = 0, st = OR_MAX_ITER;
+    if (!isfinite(chi2)) {
+        st = OR_NONFINITE;
+    } else {
+        while (it < max_iter) {
+            double delta[3], pt[3], Ht[3][3], gt[3];
+            ++it;
+            if (fano_solve(H, lambda, grad, delta) != 0) { st = OR_SINGULAR; break; }
+            pt[0] = p[0] + delta[0];
+            pt[1] = clampd(p[1] + delta[1], Alo, Ahi);
+            pt[2] = clampd(p[2] + delta[2], Blo, Bhi);
+            const double chi2t = fano_eval(x, y, T, q, gamma, pt, Ht, gt);
+            if (!isfinite(chi2t)) { lambda *= 10.0; continue; }
+            if (fabs(chi2t - chi2) <= tol * chi2) {
+                if (chi2t <= chi2) {
+                    for (int i = 0; i < 3; ++i) p[i] = pt[i];
+                    chi2 = chi2t;
+                }
+                st = OR_CONVERGED;
+                break;
+            }
+            if (chi2t < chi2) {
+                for (int i = 0; i < 3; ++i) p[i] = pt[i];
+                chi2 = chi2t;
+                memcpy(H, Ht, sizeof(H));
+                memcpy(grad, gt, sizeof(grad));
+                lambda *= 0.1;
+            } else {
+                lambda *= 10.0;
+            }
+        }
+    }
+    for (int i = 0; i < 3; ++i) p_out[i] = p[i];
+    *rss = chi2;
+    *iters = it;
+    *status = st;
+}
+
+/* Batch: p0 == NULL takes or_fano_init. */
+void or_fano_fit_batch(const double* y, int64_t n, const double* x, int T, double q, double gamma, double A_bar,
+                       double B_bar, double box, const double* p0, int max_iter, double tol, double lambda0,
+                       double* init_out, double* params, double* rss, int* iters, int* status)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double q0[3];
+        if (p0) {
+            for (int j = 0; j < 3; ++j) q0[j] = p0[3 * i + j];
+        } else {
+            or_fano_init(y + i * T, x, T, q, gamma, A_bar, B_bar, q0);
+        }
+        if (init_out)
+            for (int j = 0; j < 3; ++j) init_out[3 * i + j] = q0[j];
+        or_fano_fit(y + i * T, x, T, q, gamma, A_bar, B_bar, box, q0, max_iter, tol, lambda0, params + 3 * i,
+                    rss + i, iters + i, status + i);
+    }
+}
+
+/* Brute force for tiny inputs: least chi^2 over a grid of centres with A
+ * and B on grids inside their boxes. */
+void or_fano_grid_fit(const double* y, const double* x, int T, double q, double gamma, const double* cgrid, int nc,
+                      const double* Agrid, int nA, const double* Bgrid, int nB, double* p_best, double* chi2_best)
+{
+    double best = INFINITY;
+    double* m = (double*)malloc(sizeof(double) * (size_t)T);
+    if (!m) return;
+    for (int a = 0; a < nc; ++a)
+        for (int b = 0; b < nA; ++b)
+            for (int c = 0; c < nB; ++c) {
+                const double p[3] = { cgrid[a], Agrid[b], Bgrid[c] };
+                or_fano_model(x, T, q, gamma, p, m);
+                double chi2 = 0.0;
+                for (int k = 0; k < T; ++k) chi2 += (y[k] - m[k]) * (y[k] - m[k]);
+                if (chi2 < best) {
+                    best = chi2;
+                    for (int j = 0; j < 3; ++j) p_best[j] = p[j];
+                }
+            }
+    free(m);
     *chi2_best = best;
 }
