@@ -251,7 +251,7 @@ def grid_fit(y, x, cgrid, ggrid):
 
 
 # ---------------------------------------------------------------------------
-# The paper's Fano lineshape with box-constrained scale and offset (f1)
+# The paper's Fano lineshape with box-constrained scale and offset
 # ---------------------------------------------------------------------------
 def fano_model(x, q, gamma, p) -> np.ndarray:
     """m(x) = B + A (q + e)^2 / (1 + e^2), e = (x - c) / gamma, p = (c, A, B)."""

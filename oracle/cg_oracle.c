@@ -504,15 +504,16 @@ void or_grid_fit(const double* y, const double* x, int T,
 }
 
 /* ------------------------------------------------------------------ */
-/* The paper's fitted lineshape: a Fano profile        */
+/* The paper's fitted lineshape: a Fano profile                       */
 /* ("Data Capture and Processing", fit paragraph; Fano 1961)           */
 /*   eps = (x - c) / gamma,   F = (q + eps)^2 / (1 + eps^2),           */
 /*   m(x) = B + A F                                                    */
 /* with the centre c free, the scale A and offset B held to a box      */
 /* [lo, hi] of +-box around pre-computed averages (A_bar, B_bar), and  */
-/* the asymmetry q and width gamma fixed.  Bounds are applied by       */
-/* clamping A and B after every trial step (the constraint handling    */
-/* of the LM library the paper uses).  q = 0 gives the Lorentzian dip   */
+/* the asymmetry q and width gamma fixed.  Bounds: a parameter on a    */
+/* bound whose gradient points outward is held out of the step (an     */
+/* active set), the others take the reduced LM step, and the trial     */
+/* point is clamped onto the box.  q = 0 gives the Lorentzian dip      */
 /* B + A - A / (1 + eps^2).                                            */
 /*   dm/dc = -A F'(eps) / gamma,  F'(eps) = 2 (q+eps)(1 - q eps)/(1+eps^2)^2 */
 /*   dm/dA = F,                    dm/dB = 1                            */
@@ -563,8 +564,10 @@ static double fano_eval(const double* x, const double* y, int T, double q, doubl
     return chi2;
 }
 
-/* (H + lambda diag H) delta = grad for 3 parameters, Jacobi-scaled Cholesky */
-static int fano_solve(const double H[3][3], double lambda, const double grad[3], double delta[3])
+/* (H + lambda diag H) delta = grad for 3 parameters, Jacobi-scaled Cholesky;
+ * a parameter whose bit is set in held keeps delta = 0 and drops out of the
+ * system (its row and column are decoupled from the others). */
+static int fano_solve(const double H[3][3], double lambda, const double grad[3], int held, double delta[3])
 {
     double s[3], M[3][3], Lc[3][3], z[3], u[3];
     for (int i = 0; i < 3; ++i) {
@@ -572,7 +575,7 @@ static int fano_solve(const double H[3][3], double lambda, const double grad[3],
         s[i] = 1.0 / sqrt(H[i][i]);
     }
     for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j) M[i][j] = H[i][j] * s[i] * s[j];
+        for (int j = 0; j < 3; ++j) M[i][j] = ((held >> i) & 1) || ((held >> j) & 1) ? 0.0 : H[i][j] * s[i] * s[j];
         M[i][i] = 1.0 + lambda;
     }
     memset(Lc, 0, sizeof(Lc));
@@ -588,7 +591,7 @@ static int fano_solve(const double H[3][3], double lambda, const double grad[3],
         }
     }
     for (int i = 0; i < 3; ++i) {
-        double v = grad[i] * s[i];
+        double v = ((held >> i) & 1) ? 0.0 : grad[i] * s[i];
         for (int t = 0; t < i; ++t) v -= Lc[i][t] * z[t];
         z[i] = v / Lc[i][i];
     }
@@ -625,9 +628,21 @@ void or_fano_init(const double* y, const double* x, int T, double q, double gamm
     p0[2] = B_bar;
 }
 
+/* Bit i set when parameter i sits on a bound of its box and the gradient
+ * J^T (y - m) points out of the box there (moving it inward cannot lower
+ * chi^2 to first order): it is held for this step. */
+static int fano_held(const double p[3], const double grad[3], double Alo, double Ahi, double Blo, double Bhi)
+{
+    int h = 0;
+    if ((p[1] <= Alo && grad[1] < 0.0) || (p[1] >= Ahi && grad[1] > 0.0)) h |= 2;
+    if ((p[2] <= Blo && grad[2] < 0.0) || (p[2] >= Bhi && grad[2] > 0.0)) h |= 4;
+    return h;
+}
+
 /* Box-constrained Levenberg-Marquardt of one spectrum, p = (c, A, B):
- * trial = clamp(p + delta) onto the box; accept / reject, lambda and the
- * stopping rule as in or_lm_fit. */
+ * the parameters held by fano_held stay where they are, the others take the
+ * damped step of the reduced system, and the trial point is clamped onto the
+ * box; accept / reject, lambda and the stopping rule as in or_lm_fit. */
 void or_fano_fit(const double* y, const double* x, int T, double q, double gamma, double A_bar, double B_bar,
                  double box, const double* p0, int max_iter, double tol, double lambda0, double* p_out,
                  double* rss, int* iters, int* status)
@@ -648,7 +663,10 @@ void or_fano_fit(const double* y, const double* x, int T, double q, double gamma
         while (it < max_iter) {
             double delta[3], pt[3], Ht[3][3], gt[3];
             ++it;
-            if (fano_solve(H, lambda, grad, delta) != 0) { st = OR_SINGULAR; break; }
+            if (fano_solve(H, lambda, grad, fano_held(p, grad, Alo, Ahi, Blo, Bhi), delta) != 0) {
+                st = OR_SINGULAR;
+                break;
+            }
             pt[0] = p[0] + delta[0];
             pt[1] = clampd(p[1] + delta[1], Alo, Ahi);
             pt[2] = clampd(p[2] + delta[2], Blo, Bhi);

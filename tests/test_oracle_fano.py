@@ -85,3 +85,44 @@ def test_lowest_value_initial_guess():
     p0 = oracle.fano_init(y, X, q, GAMMA, 0.7, 0.3)
     assert p0[0] == pytest.approx(c, abs=1e-6)
     assert (p0[1], p0[2]) == (0.7, 0.3)
+
+
+def _kkt(y, x, q, p, lo, hi):
+    """Normalised gradient J^T (y - m) / sqrt(diag(J^T J) chi2) at p, and which
+    of A, B sit on a bound."""
+    r = y - oracle.fano_model(x, q, GAMMA, p)
+    J = oracle.fano_jacobian(x, q, GAMMA, p)
+    g = J.T @ r / np.sqrt(np.sum(J * J, axis=0) * np.sum(r * r))
+    at_lo = np.array([False, p[1] <= lo[0], p[2] <= lo[1]])
+    at_hi = np.array([False, p[1] >= hi[0], p[2] >= hi[1]])
+    return g, at_lo, at_hi
+
+
+@pytest.mark.parametrize("fa,fb", [(1.0, 1.0), (1.3, 1.0), (1.0, 0.8), (0.8, 1.25), (1.25, 1.25)])
+def test_box_constrained_optimum_satisfies_kkt(fa, fb):
+    # Karush-Kuhn-Tucker conditions of min chi^2 over the box: zero gradient
+    # in the free coordinates, gradient pointing out of the box on a bound
+    rng = np.random.default_rng(5)
+    q = 0.3
+    y = oracle.fano_model(X, q, GAMMA, [3.1e6, 0.7 * fa, 0.3 * fb]) + 0.004 * rng.standard_normal(X.size)
+    r = oracle.fano_fit_batch(y, X, q, GAMMA, 0.7, 0.3, box=0.1, converged=True)
+    p = r["params"][0]
+    g, at_lo, at_hi = _kkt(y, X, q, p, (0.63, 0.27), (0.77, 0.33))
+    free = ~(at_lo | at_hi)
+    assert np.all(np.abs(g[free]) <= 1e-7), g
+    assert np.all(g[at_lo] <= 0.0) and np.all(g[at_hi] >= 0.0), (g, at_lo, at_hi)
+    # data inside the box leave it free; data outside put a bound in play
+    assert bool(np.any(at_lo | at_hi)) == ((fa, fb) != (1.0, 1.0))
+
+
+@pytest.mark.parametrize("fa,fb", [(1.3, 1.0), (1.0, 0.8), (0.8, 1.25), (1.25, 1.25)])
+def test_active_bounds_converge_within_the_papers_iterations(fa, fb):
+    # holding a bound parameter out of the step keeps the centre's step
+    # consistent; the fit settles within the paper's 20 iterations at tol 1e-6
+    rng = np.random.default_rng(6)
+    q = -0.5
+    y = oracle.fano_model(X, q, GAMMA, [-8e6, 0.7 * fa, 0.3 * fb]) + 0.004 * rng.standard_normal(X.size)
+    r20 = oracle.fano_fit_batch(y, X, q, GAMMA, 0.7, 0.3, box=0.1, max_iter=20, tol=1e-6)
+    rc = oracle.fano_fit_batch(y, X, q, GAMMA, 0.7, 0.3, box=0.1, converged=True)
+    assert r20["status"][0] == 0 and r20["iters"][0] <= 20
+    assert abs(r20["params"][0, 0] - rc["params"][0, 0]) <= 1e-4 * 2 * GAMMA
