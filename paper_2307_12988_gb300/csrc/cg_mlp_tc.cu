@@ -27,7 +27,6 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
@@ -62,12 +61,17 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
     return false;
 }
 
+// GELU in its tanh form, evaluated as z / (1 + exp(-2 k (z + c z^3))), since
+// 0.5 (1 + tanh(v)) = 1 / (1 + exp(-2 v)).  Unlike 1 + tanh, which cancels
+// for negative z (an absolute tanh error of 2^-11 there shifted the trained
+// network's outputs by 7 % of their scale), the quotient keeps its relative
+// accuracy over the whole range; exp(+large) = inf gives the limit 0.
 __device__ __forceinline__ float gelu_fast(float z)
 {
-    const float u = 0.7978845608028654f * fmaf(0.044715f * z * z, z, z);
-    float t;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
-    return 0.5f * z * (1.0f + t);
+    const float v = fmaf(0.044715f * z * z, z, z);
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-2.0f * 0.7978845608028654f * 1.4426950408889634f * v));
+    return __fdividef(z, 1.0f + e);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
@@ -76,23 +80,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// GELU of two pre-activations evaluated in FP16x2 (tanh form), returned as
-// the BF16 pair the next layer's MMA reads; FP16's 11-bit significand is
-// finer than the BF16 result.  Inputs beyond the FP16 range saturate the
-// tanh and give the GELU's limits.
+// GELU of two pre-activations as the BF16 pair the next layer's MMA reads.
 __device__ __forceinline__ uint32_t gelu_bf16x2(float z0, float z1)
 {
-    const __half2 z = __floats2half2_rn(z0, z1);
-    const __half2 z2 = __hmul2(z, z);
-    const __half2 inner = __hfma2(z2, __float2half2_rn(0.7978845608028654f * 0.044715f),
-                                  __float2half2_rn(0.7978845608028654f));
-    const __half2 u = __hmul2(z, inner);
-    __half2 t;
-    asm("tanh.approx.f16x2 %0, %1;" : "=r"(*reinterpret_cast<uint32_t*>(&t)) : "r"(*reinterpret_cast<const uint32_t*>(&u)));
-    const __half2 hz = __hmul2(z, __float2half2_rn(0.5f));
-    const __half2 g = __hfma2(hz, t, hz);
-    const float2 gf = __half22float2(g);
-    return pack_bf16(gf.x, gf.y);
+    return pack_bf16(gelu_fast(z0), gelu_fast(z1));
 }
 
 // byte offset of BF16 element (row, k) in a swizzled operand tile

@@ -5,7 +5,8 @@ step are compared with oracle/mlp.py on the same parameters and data;
 training is deterministic and lowers the loss.  Inference kernel (tcgen05,
 BF16 operands, FP32 accumulation): compared with the reference evaluated on
 the same BF16-rounded operands (input, W1, the first hidden layer, W2), so
-the remaining difference is accumulation order and the hardware tanh.
+the remaining difference is accumulation order and the hardware exponential;
+random networks at ragged sizes and the shipped trained network.
 Pipeline: with a network whose guess never converges in the polish steps,
 every frame falls back to the full LM from the moment guess and must then
 match the moment-guess plan bit for bit.
@@ -129,6 +130,34 @@ def test_inference_kernel_matches_rounded_oracle(geom, n):
     x_scale = np.mean(np.diff(geom.tooth_x))
     want[:, 1] = np.clip(np.abs(want[:, 1]), 0.5 * x_scale, 0.5 * (T - 1) * x_scale)
     # in the network's standardised output units
+    err = np.max(np.abs((p0 - want) / out_scale))
+    assert err <= 2e-3 * max(1.0, np.max(np.abs(o))), err
+
+
+@pytest.mark.parametrize("n", [130, 1000])
+def test_trained_network_inference_matches_rounded_oracle(n):
+    # the trained network's hidden pre-activations reach |z| ~ 20, with many
+    # strongly negative; a GELU that cancels there fails this bar
+    import os
+    w = synth.WIDE
+    path = os.path.join(os.path.dirname(cg.__file__), "data", "mlp_wide_t221.cgmlp")
+    blob = open(path, "rb").read()
+    hdr = np.frombuffer(blob[8:24], dtype=np.int32)
+    n_in, H, n_out = int(hdr[0]), int(hdr[1]), int(hdr[2])
+    f32 = np.frombuffer(blob[24:], dtype=np.float32).astype(np.float64)
+    in_mean, in_scale = f32[:n_in], f32[n_in:2 * n_in]
+    out_mean, out_scale = f32[2 * n_in:2 * n_in + 4], f32[2 * n_in + 4:2 * n_in + 8]
+    theta = f32[2 * n_in + 8:]
+    ys = synth.tooth_domain_spectra(w, n, seed=11)["y"].astype(np.float32)
+    with _plan(w, init=cg.INIT_MLP) as plan:
+        plan.mlp_load(blob)
+        p0 = plan.mlp_infer(_dev(ys)).cpu().numpy().astype(np.float64)
+        cg.cg_check_device(plan.handle)
+    xs = ((ys - in_mean.astype(np.float32)) * in_scale.astype(np.float32)).astype(np.float32).astype(np.float64)
+    o = omlp.forward(theta, xs, n_in, H, n_out, operand_round=omlp.bf16_round)
+    want = o * out_scale + out_mean
+    dx = np.mean(np.diff(w.tooth_x))
+    want[:, 1] = np.clip(np.abs(want[:, 1]), 0.5 * dx, 0.5 * (n_in - 1) * dx)
     err = np.max(np.abs((p0 - want) / out_scale))
     assert err <= 2e-3 * max(1.0, np.max(np.abs(o))), err
 
