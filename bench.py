@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fitted spectra/s & input GB/s vs HBM peak at fixed fit error; p99 frame-to-fit"
 FWHM_HZ = 80e6
+FANO_Q = 0.3                 # asymmetry of the Fano workload's lineshape
 
 
 def _peaks():
@@ -134,7 +135,43 @@ GEOMETRIES = {
     "serve4096": ("SERVE_4096", dict(snr_db=30.0, center_amp_hz=20e6)),
     # the paper's digitiser frame: 8-bit samples at 2.2 GS/s, 2200 per frame
     "paper8": ("PAPER_8BIT", dict(snr_db=30.0, center_amp_hz=20e6, bits=8)),
+    # the paper's fitted lineshape: Fano profile (q = 0.3, FWHM 80 MHz, depth 0.7)
+    # at the paper rate, fitted with the centre free, scale and offset boxed
+    "fano": ("PAPER_RATE", dict(snr_db=30.0, center_amp_hz=20e6, shape="fano", fano_q=FANO_Q)),
 }
+
+
+def fano_opts(args) -> dict:
+    """Plan options of the Fano workload: q and gamma fixed at the generator's
+    values, scale and offset boxed +-10 % around the lineshape's 0.7 / 0.3."""
+    if args.workload != "fano":
+        return {}
+    import paper_2307_12988_gb300 as cg
+    return dict(model=cg.MODEL_FANO, fano_q=FANO_Q, fano_gamma=FWHM_HZ / 2.0, fano_A=0.7, fano_B=0.3,
+                fano_box=0.1)
+
+
+FIT_DESC = {False: "moment init, 20-iteration LM",
+            True: "lowest-tooth init, 20-iteration box-constrained Fano LM"}
+
+
+def oracle_fit(y, x, args, converged=False):
+    """The oracle's fit of the workload's model on spectra y."""
+    import oracle
+    if args.workload == "fano":
+        r = oracle.fano_fit_batch(y, x, FANO_Q, FWHM_HZ / 2.0, 0.7, 0.3, box=0.1, converged=converged)
+        return dict(r, params=np.column_stack([r["params"][:, 0], np.full(len(y), FWHM_HZ / 2.0),
+                                               r["params"][:, 1:]]))
+    return oracle.fit_batch(y, x, converged=converged)
+
+
+def oracle_process(frames, bins, ref, x, args):
+    """The oracle's whole path (readout, initial guess, LM) for the workload."""
+    import oracle
+    if args.workload == "fano":
+        _, y = oracle.readout(frames, bins, ref)
+        return oracle_fit(y, x, args)
+    return oracle.process(frames, bins, ref, x)
 
 
 def workload_name(args, n):
@@ -174,6 +211,9 @@ NCU_TRAFFIC_PER_FRAME = {("paper_rate", "fft", "moment"): {"readout": 2518.8, "i
 # FP32 operations of one LM point evaluation (model, residual, Jacobian and
 # the 14 running sums of J^T J, J^T r and chi^2): 11 + 10 FMA x 2 + 4 adds
 LM_FLOP_PER_POINT = 35
+# the Fano model's point: e, 1 + e^2, its reciprocal, (q + e)^2 / (1 + e^2),
+# the residual, dm/dc (7) and 9 running sums (6 FMA + 3 adds)
+LM_FLOP_PER_POINT_FANO = 33
 
 
 def kernel_rooflines(stage_ms, stage_launches, n, g, T, args, mean_iters, hbm, bf16):
@@ -199,7 +239,8 @@ def kernel_rooflines(stage_ms, stage_launches, n, g, T, args, mean_iters, hbm, b
             f = 2.0 * (T * 256 + 256 * 256) * frames
             r.update(bound="tensor", achieved=f / per / 1e12, peak=bf16, unit="TFLOP/s")
         elif st == "fit":
-            f = LM_FLOP_PER_POINT * T * (mean_iters + 1.0) * frames
+            fp = LM_FLOP_PER_POINT_FANO if args.workload == "fano" else LM_FLOP_PER_POINT
+            f = fp * T * (mean_iters + 1.0) * frames
             r.update(bound="alu", achieved=f / per / 1e12, peak=alu_peak, unit="TFLOP/s")
         if "achieved" in r:
             r["frac"] = r["achieved"] / r["peak"]
@@ -219,21 +260,21 @@ def cpu_baseline_leg(frames, params, status, iters, plan, ref, g, args) -> dict:
     bins, x = plan.bins, g.tooth_x
     probe = min(512, frames_host.shape[0])
     t = time.perf_counter()
-    oracle.process(frames_host[:probe], bins, ref, x)
+    oracle_process(frames_host[:probe], bins, ref, x, args)
     dt = time.perf_counter() - t
     n = int(min(frames_host.shape[0], max(probe, probe * args.cpu_seconds / max(dt, 1e-6))))
     t = time.perf_counter()
-    oracle.process(frames_host[:n], bins, ref, x)
+    oracle_process(frames_host[:n], bins, ref, x, args)
     dt = time.perf_counter() - t
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     cpu = {"value": n / dt, "unit": "spectra/s", "cores": cores, "kind": "oracle",
            "sample": f"first {n} of the workload's frames (FP64 direct-sum DFT at the "
-                     f"{g.n_teeth} teeth, moment init, 20-iteration LM), {dt:.1f} s"}
+                     f"{g.n_teeth} teeth, {FIT_DESC[args.workload == 'fano']}), {dt:.1f} s"}
     rng = np.random.default_rng(7)
     idx = np.sort(rng.choice(frames_host.shape[0], size=min(256, frames_host.shape[0]),
                              replace=False))
-    o = oracle.process(frames_host[idx], bins, ref, x)
-    conv = oracle.fit_batch(o["y"], x, converged=True)
+    _, y_idx = oracle.readout(frames_host[idx], bins, ref)
+    conv = oracle_fit(y_idx, x, args, converged=True)
     dc = np.abs(p_host[idx, 0] - conv["params"][:, 0])
     st = status.cpu().numpy()
     fe = {"frames_checked": int(idx.size), "center_err_max_hz": float(dc.max()),
@@ -268,7 +309,7 @@ def run_ours(args):
                             "fold": cg.READOUT_FOLD_GEMM}[args.readout],
                    sample_bits=args.sample_bits,
                    init=(cg.INIT_MLP if args.init == "mlp" else cg.INIT_MOMENT),
-                   polish_iter=args.polish)
+                   polish_iter=args.polish, **fano_opts(args))
     if args.init == "mlp":
         with open(MLP_BLOB, "rb") as f:
             plan.mlp_load(f.read())
@@ -338,7 +379,9 @@ def run_ours(args):
                    "l2": f"inputs ({sb * g.frame_len * n / 1e9:.1f} GB) larger than L2; no flush",
                    "lanes_per_frame": plan.info["lanes_per_frame"],
                    "path": ["auto", "fused", "split", "pipeline"][plan.info["path"]],
-                   "fft_len": plan.info["fft_len"], "readout": args.readout, "init": args.init,
+                   "fft_len": plan.info["fft_len"], "readout": args.readout,
+                   "init": "lowest tooth" if args.workload == "fano" else args.init,
+                   "model": "fano" if args.workload == "fano" else "lorentz",
                    "polish_iter": args.polish if args.init == "mlp" else None},
         "input_gbs": total_frames * sb * g.frame_len / (ms_step / 1e3) / 1e9,
         "roofline": {"kernel": dominant, "bound": dom.get("bound"), "achieved": dom.get("achieved"),

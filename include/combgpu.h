@@ -71,6 +71,20 @@ typedef enum cg_status {
 enum { CG_READOUT_FFT = 0, CG_READOUT_GEMM_SPLIT = 1, CG_READOUT_FOLD_GEMM = 2 };
 enum { CG_FFT_AUTO = 0, CG_FFT_FULL = 1, CG_FFT_COSET = 2 };
 enum { CG_INIT_MOMENT = 0, CG_INIT_MLP = 1 };
+/* Fitted lineshape.  LORENTZ: m = B + A g^2 / ((x - c)^2 + g^2), all four
+   parameters free.  FANO (the paper's fit, "Data Capture and Processing"):
+   m = B + A (q + e)^2 / (1 + e^2), e = (x - c) / gamma, with the centre c
+   free, the scale A and offset B held to fano_box (e.g. 0.1 = +-10 %) around
+   the pre-computed averages fano_A, fano_B, the asymmetry q and width gamma
+   fixed.  Bounds: A or B on a bound with the gradient pointing outward is
+   held out of that LM step (active set), the others take the reduced step,
+   and the trial point is clamped onto the box.  The initial centre
+   is the lowest tooth moved by q gamma (where the profile's minimum lies).
+   params_dev then holds (c, gamma, A, B).  A Fano plan refuses init =
+   CG_INIT_MLP (CG_ERR_UNSUPPORTED), runs its fit in two or more lanes per
+   frame, and cg_plan fails with CG_ERR_UNSUPPORTED when no Fano kernel
+   covers n_teeth at the requested lanes_per_frame. */
+enum { CG_MODEL_LORENTZ = 0, CG_MODEL_FANO = 1 };
 /* Kernel arrangement of cg_process. */
 enum {
     CG_PATH_AUTO = 0,      /* PIPELINE when the fit kernels cover n_teeth, else FUSED */
@@ -105,7 +119,14 @@ typedef struct cg_opts {
     int polish_iter;      /* CG_INIT_MLP: LM trial steps from the learned initial
                              guess before a frame falls back to the full LM from
                              the moment guess; 0 = 2 */
-    int reserved[4];      /* must be zero */
+    int model;            /* CG_MODEL_LORENTZ (default) or CG_MODEL_FANO (pipeline
+                             path, moment-free: the Fano fit makes its own guess) */
+    int reserved[3];      /* must be zero */
+    double fano_q;        /* CG_MODEL_FANO: asymmetry q (fixed) */
+    double fano_gamma;    /* CG_MODEL_FANO: width gamma in abscissa units (fixed, > 0) */
+    double fano_A;        /* CG_MODEL_FANO: average scale A (box centre, != 0) */
+    double fano_B;        /* CG_MODEL_FANO: average offset B (box centre) */
+    double fano_box;      /* CG_MODEL_FANO: relative half-width of the A and B boxes (>= 0) */
 } cg_opts;
 
 typedef struct cg_plan_s* cg_plan_t;
@@ -206,7 +227,8 @@ cg_status cg_readout_i8(cg_plan_t plan, const int8_t* frames_dev, int64_t n_fram
 /*
  * cg_fit -- only the initial guess and LM fit of cg_process, on normalised
  * spectra y_dev float [n][T].  p0_dev float [n][4] (abscissa units) or NULL
- * for the moment initial guess.  Outputs as in cg_process.
+ * for the moment initial guess (CG_MODEL_FANO: not read; the fit makes its
+ * own guess).  Outputs as in cg_process.
  */
 cg_status cg_fit(cg_plan_t plan, const float* y_dev, int64_t n, const float* p0_dev,
                  float* params_dev, float* rss_dev, int16_t* iters_dev,

@@ -26,7 +26,7 @@ from ._binding import (RESULT_DTYPE, INJECT_FAIL_LAUNCH, INJECT_HOLD, INJECT_THR
 from ._binding import (FFT_AUTO, FFT_COSET, FFT_FULL, FIT_CONVERGED, FIT_FALLBACK, FIT_INIT_FLAT,
                        FIT_MAX_ITER, FIT_NONFINITE, FIT_SINGULAR, INIT_MLP, INIT_MOMENT,
                        READOUT_FFT, READOUT_GEMM_SPLIT, READOUT_FOLD_GEMM, PATH_AUTO, PATH_FUSED, PATH_SPLIT,
-                       PATH_PIPELINE)
+                       PATH_PIPELINE, MODEL_LORENTZ, MODEL_FANO)
 
 __all__ = ["Plan", "Mlp", "Server", "Stream", "CgError", "load", "cg_plan", "cg_plan_destroy", "cg_plan_describe",
            "cg_process", "cg_readout", "cg_fit", "cg_reference_accumulate",

@@ -32,6 +32,7 @@ READOUT_FFT, READOUT_GEMM_SPLIT, READOUT_FOLD_GEMM = 0, 1, 2
 FFT_AUTO, FFT_FULL, FFT_COSET = 0, 1, 2
 INIT_MOMENT, INIT_MLP = 0, 1
 PATH_AUTO, PATH_FUSED, PATH_SPLIT, PATH_PIPELINE = 0, 1, 2, 3
+MODEL_LORENTZ, MODEL_FANO = 0, 1
 
 
 class CgError(RuntimeError):
@@ -48,7 +49,10 @@ class cg_opts(ctypes.Structure):
                 ("lambda0", ctypes.c_double), ("lanes_per_frame", ctypes.c_int),
                 ("path", ctypes.c_int), ("chunk_frames", ctypes.c_int),
                 ("sample_bits", ctypes.c_int), ("solve_f64", ctypes.c_int),
-                ("polish_iter", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("polish_iter", ctypes.c_int), ("model", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3), ("fano_q", ctypes.c_double),
+                ("fano_gamma", ctypes.c_double), ("fano_A", ctypes.c_double),
+                ("fano_B", ctypes.c_double), ("fano_box", ctypes.c_double)]
 
 
 class cg_plan_info(ctypes.Structure):

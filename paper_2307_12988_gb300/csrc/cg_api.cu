@@ -244,9 +244,11 @@ cudaError_t setup_fit_kernels(cg_plan_s* p)
         else
             G = T <= 48 ? 1 : (T <= 100 ? 2 : 4);
     }
+    const int model = p->opts.model;
+    if (model == CG_MODEL_FANO && G == 1) G = 2;   // the Fano fit runs in the register-resident kernel
     bool exact = false;
-    int ppl = cg::fit2_ppl(G, T, &exact);
-    while (ppl == 0 && G < 32 && !p->opts.lanes_per_frame) ppl = cg::fit2_ppl(G *= 2, T, &exact);
+    int ppl = cg::fit2_ppl(G, T, &exact, model);
+    while (ppl == 0 && G < 32 && !p->opts.lanes_per_frame) ppl = cg::fit2_ppl(G *= 2, T, &exact, model);
     if (ppl == 0) return cudaSuccess;
     const int npad = cg::init_npad(p->n_outer);
     if (npad == 0) return cudaSuccess;
@@ -268,8 +270,8 @@ cudaError_t setup_fit_kernels(cg_plan_s* p)
     p->init_smem = 4 * ((2 * T + p->n_outer + 3) & ~3) + 8 * 2 * 4 + 4 * 4 * 2 * 32 * ia.row_stride;
     cudaError_t e;
     int occ = 0;
-    void* ff = cg::fit2_ptr(G, ppl, exact);
-    const size_t fsm = cg::fit2_smem(G, T);
+    void* ff = cg::fit2_ptr(G, ppl, exact, model);
+    const size_t fsm = cg::fit2_smem(G, T, model);
     if ((e = cg::raise_smem_limit(ff, static_cast<int>(fsm))) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ff, cg::fit2_threads(G), fsm)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&p->d.fit_counter, sizeof(unsigned long long))) != cudaSuccess) return e;
@@ -363,6 +365,8 @@ void cg_opts_default(cg_opts* o)
     o->chunk_frames = 0;
     o->sample_bits = 16;
     o->solve_f64 = -1;
+    o->model = CG_MODEL_LORENTZ;
+    o->fano_box = 0.1;
 }
 
 const char* cg_status_string(cg_status s)
@@ -414,6 +418,16 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
     if (o.init != CG_INIT_MOMENT && o.init != CG_INIT_MLP) return fail(CG_ERR_ARG, "init must be CG_INIT_MOMENT or CG_INIT_MLP");
     if (o.polish_iter < 0 || o.polish_iter > 32767) return fail(CG_ERR_ARG, "polish_iter outside [0, 32767]");
     if (o.polish_iter == 0) o.polish_iter = 2;
+    if (o.model != CG_MODEL_LORENTZ && o.model != CG_MODEL_FANO)
+        return fail(CG_ERR_ARG, "model must be CG_MODEL_LORENTZ or CG_MODEL_FANO");
+    if (o.model == CG_MODEL_FANO) {
+        if (!(o.fano_gamma > 0.0) || !std::isfinite(o.fano_gamma)) return fail(CG_ERR_ARG, "fano_gamma must be > 0");
+        if (!(o.fano_A != 0.0) || !std::isfinite(o.fano_A) || !std::isfinite(o.fano_B) || !std::isfinite(o.fano_q))
+            return fail(CG_ERR_ARG, "fano_A (nonzero), fano_B and fano_q must be finite");
+        if (!(o.fano_box >= 0.0) || !(o.fano_box < 1.0)) return fail(CG_ERR_ARG, "fano_box must be in [0, 1)");
+        if (o.init != CG_INIT_MOMENT)
+            return fail(CG_ERR_UNSUPPORTED, "the Fano model makes its own initial guess (init must be CG_INIT_MOMENT)");
+    }
     for (size_t i = 0; i < sizeof(o.reserved) / sizeof(o.reserved[0]); ++i)
         if (o.reserved[i] != 0) return fail(CG_ERR_ARG, "reserved option fields must be zero");
 
@@ -622,6 +636,10 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
                         "n_teeth <= 128 and the fit kernels");
         }
     }
+    if (o.model == CG_MODEL_FANO && !p->fit_ok) {
+        free_plan(p);
+        return fail(CG_ERR_UNSUPPORTED, "no Fano fit kernel for this n_teeth and lanes_per_frame");
+    }
     if (o.init == CG_INIT_MLP && (!p->fit_ok || T > 256)) {
         free_plan(p);
         return fail(CG_ERR_UNSUPPORTED, "the learned initial guess needs the fit kernels and n_teeth <= 256");
@@ -658,7 +676,8 @@ cg_status cg_plan_describe(cg_plan_t p, cg_plan_info* info, int* bins_host)
     info->n_collisions = p->n_collisions;
     info->path = (p->opts.path == CG_PATH_AUTO) ? (p->fit_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED)
                : (p->opts.path == CG_PATH_PIPELINE && !p->fit_ok) ? CG_PATH_FUSED : p->opts.path;
-    if (p->opts.readout != CG_READOUT_FFT || p->opts.init == CG_INIT_MLP) info->path = CG_PATH_PIPELINE;
+    if (p->opts.readout != CG_READOUT_FFT || p->opts.init == CG_INIT_MLP || p->opts.model == CG_MODEL_FANO)
+        info->path = CG_PATH_PIPELINE;
     if (info->path == CG_PATH_PIPELINE) info->lanes_per_frame = p->G2;
     if (bins_host) std::memcpy(bins_host, p->bins.data(), sizeof(int) * p->T);
     return CG_OK;
@@ -719,7 +738,8 @@ static cg_status process_impl(cg_plan_t p, const void* frames, int sbytes, int64
     if (path == CG_PATH_AUTO) path = p->fit_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED;
     if (path == CG_PATH_PIPELINE && !p->fit_ok) path = CG_PATH_FUSED;
     // tensor-core readouts or learned guess: readout, then guess and fit kernels
-    if (p->opts.readout != CG_READOUT_FFT || mlp || sbytes == 1) path = CG_PATH_PIPELINE;
+    const bool fano = p->opts.model == CG_MODEL_FANO;
+    if (p->opts.readout != CG_READOUT_FFT || mlp || sbytes == 1 || fano) path = CG_PATH_PIPELINE;
     const bool fast = !gemm && !fold && p->fast_ok && aligned4;
     const bool pow2 = !gemm && !fold && !fast && p->pow2_ok && aligned4;
     if (path == CG_PATH_PIPELINE) {
@@ -762,7 +782,7 @@ static cg_status process_impl(cg_plan_t p, const void* frames, int sbytes, int64
             });
             if (e == cudaSuccess && mlp)
                 e = timed(p, CG_STAGE_MLP, p->s_read, [&] { return cg::launch_mlp(p, yc, ac, m, pc, sc, p->s_read); });
-            else if (e == cudaSuccess)
+            else if (e == cudaSuccess && !fano)
                 e = timed(p, CG_STAGE_INIT, p->s_read,
                           [&] { return cg::launch_init(p, yc, ac, m, pc, sc, p->s_read, nullptr, nullptr); });
             if (e == cudaSuccess) e = cudaEventRecord(p->ev_read, p->s_read);
@@ -873,7 +893,12 @@ cg_status cg_fit(cg_plan_t p, const float* y, int64_t n, const float* p0, float*
     if (n < 0) return fail(CG_ERR_ARG, "n < 0");
     if (n == 0) return CG_OK;
     if (!y || !params) return fail(CG_ERR_ARG, "y_dev and params_dev are required");
-    cudaError_t e = cg::launch_fit(p, y, nullptr, n, p0, params, rss, iters, status, static_cast<cudaStream_t>(stream));
+    cudaError_t e;
+    if (p->opts.model == CG_MODEL_FANO)   // the Fano fit makes its own guess; p0 is not read
+        e = cg::launch_fit2(p, y, nullptr, n, nullptr, nullptr, params, rss, iters, status,
+                            static_cast<cudaStream_t>(stream));
+    else
+        e = cg::launch_fit(p, y, nullptr, n, p0, params, rss, iters, status, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "cg_fit launch");
     return CG_OK;
 }

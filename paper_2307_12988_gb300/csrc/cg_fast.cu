@@ -20,6 +20,7 @@
 //
 // Paper: "Data Capture and Processing" (cast on the GPU, FFT per 1 us row,
 // tooth selection and mapping, reference normalisation, LM fit).
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -460,7 +461,7 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
 // queue.  EXACT: PPL == ceil(T / G), so only the last point of a lane can lie
 // beyond T.
 // ---------------------------------------------------------------------------
-template <int G, int PPL, bool EXACT>
+template <int G, int PPL, bool EXACT, int MODEL>
 __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kernel(Fit2Args a)
 {
     extern __shared__ __align__(16) float fsm[];
@@ -544,12 +545,42 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
         }
         // p, flag, lambda and counters of a frame that starts now
         auto start_frame = [&]() {
-            const float* q = a.p0 + fr * 4;
-            p[0] = (q[0] - a.x_mid) * inv_scale;
-            p[1] = q[1] * inv_scale;
-            p[2] = q[2];
-            p[3] = q[3];
-            flag = a.flags_in ? (a.flags_in[fr] & kInitFlat) : 0;
+            if constexpr (MODEL == 1) {
+                // lowest tooth of the group's frame (first on ties), then the
+                // profile's minimum (e = -q) moved onto the centre
+                float best = INFINITY;
+                int bk = 0x7fffffff;
+#pragma unroll
+                for (int j = 0; j < PPL; ++j) {
+                    const int k = gl + G * j;
+                    if (((EXACT && j < PPL - 1) || k < T) && yv[j] < best) {
+                        best = yv[j];
+                        bk = k;
+                    }
+                }
+                const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << leader_lane);
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) {
+                    const float ob = __shfl_xor_sync(gmask, best, o);
+                    const int ok2 = __shfl_xor_sync(gmask, bk, o);
+                    if (ob < best || (ob == best && ok2 < bk)) {
+                        best = ob;
+                        bk = ok2;
+                    }
+                }
+                p[0] = (bk < T ? us[bk] : 0.f) + a.fano_shift;
+                p[1] = a.fano_g;
+                p[2] = fminf(fmaxf(a.fano_A0, a.fano_Alo), a.fano_Ahi);
+                p[3] = fminf(fmaxf(a.fano_B0, a.fano_Blo), a.fano_Bhi);
+                flag = 0;
+            } else {
+                const float* q = a.p0 + fr * 4;
+                p[0] = (q[0] - a.x_mid) * inv_scale;
+                p[1] = q[1] * inv_scale;
+                p[2] = q[2];
+                p[3] = q[3];
+                flag = a.flags_in ? (a.flags_in[fr] & kInitFlat) : 0;
+            }
             lambda = a.lambda0;
             it = 0;
             st = kMaxIter;
@@ -599,21 +630,46 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
         const bool trial = (f >= 0 && !fresh);
         float delta[4] = {0.f, 0.f, 0.f, 0.f};
         bool ok = true;
+        // the solve of the model's free parameters (Fano: c, A, B into delta[0..2])
+        auto solve = [&](bool f64) -> bool {
+            if constexpr (MODEL == 1) {
+                // a scale or offset on its bound with the gradient pointing
+                // outward is held for this step (active set)
+                int held = 0;
+                if ((p[2] <= a.fano_Alo && Nm.b[1] < 0.f) || (p[2] >= a.fano_Ahi && Nm.b[1] > 0.f)) held |= 2;
+                if ((p[3] <= a.fano_Blo && Nm.b[2] < 0.f) || (p[3] >= a.fano_Bhi && Nm.b[2] > 0.f)) held |= 4;
+                float d3[3] = {0.f, 0.f, 0.f};
+                const bool r = f64 ? lm_solve3<double>(Nm, lambda, held, d3) : lm_solve3<float>(Nm, lambda, held, d3);
+                delta[0] = d3[0];
+                delta[1] = d3[1];
+                delta[2] = d3[2];
+                return r;
+            } else {
+                return f64 ? lm_solve4_f64(Nm, lambda, delta) : lm_solve4_fast(Nm, lambda, delta);
+            }
+        };
         if (G > 1 && a.solve_f64) {
             // FP64 is scarce: the group's leader solves, the group takes its step
             int okl = 0;
-            if (trial && gl == 0) okl = lm_solve4_f64(Nm, lambda, delta) ? 1 : 0;
+            if (trial && gl == 0) okl = solve(true) ? 1 : 0;
             okl = __shfl_sync(kFull, okl, leader_lane);
 #pragma unroll
             for (int i = 0; i < 4; ++i) delta[i] = __shfl_sync(kFull, delta[i], leader_lane);
             ok = okl != 0;
         } else if (trial) {
-            ok = a.solve_f64 ? lm_solve4_f64(Nm, lambda, delta) : lm_solve4_fast(Nm, lambda, delta);
+            ok = solve(a.solve_f64 != 0);
         }
         if (trial) {
             if (ok) {
+                if constexpr (MODEL == 1) {
+                    // c steps freely; A and B are clamped onto their boxes
+                    pe[0] = p[0] + delta[0];
+                    pe[2] = fminf(fmaxf(p[2] + delta[1], a.fano_Alo), a.fano_Ahi);
+                    pe[3] = fminf(fmaxf(p[3] + delta[2], a.fano_Blo), a.fano_Bhi);
+                } else {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) pe[i] = p[i] + delta[i];
+                    for (int i = 0; i < 4; ++i) pe[i] = p[i] + delta[i];
+                }
             } else {
                 st = kSingular;
                 done = true;
@@ -627,10 +683,21 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
 #pragma unroll
         for (int j = 0; j < PPL; ++j) {
             const int k = gl + G * j;
-            if ((EXACT && j < PPL - 1) || k < T) accum_point(us[k], yv[j], pe[0], g2, pe[2], pe[3], S);
+            if ((EXACT && j < PPL - 1) || k < T) {
+                if constexpr (MODEL == 1)
+                    accum_point_fano(us[k], yv[j], pe[0], a.fano_inv_g, a.fano_q, pe[2], pe[3], S);
+                else
+                    accum_point(us[k], yv[j], pe[0], g2, pe[2], pe[3], S);
+            }
         }
         if constexpr (G > 1) reduce_sums<G>(S);
         // ---- LM bookkeeping ----
+        auto normal = [&](const LmSums& Sx, const float (&px)[4], Normal& N) {
+            if constexpr (MODEL == 1)
+                make_normal_fano(Sx, T, N);
+            else
+                make_normal_fast(Sx, px[1], px[2], T, N);
+        };
         if (f >= 0 && !done) {
             const float chi2t = S.v[13];
             if (fresh) {
@@ -639,7 +706,7 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
                     st = kNonfinite;
                     done = true;
                 } else {
-                    make_normal_fast(S, pe[1], pe[2], T, Nm);
+                    normal(S, pe, Nm);
                     if (a.max_iter <= 0) done = true;
                 }
             } else {
@@ -658,7 +725,7 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
 #pragma unroll
                     for (int i = 0; i < 4; ++i) p[i] = pe[i];
                     chi2 = chi2t;
-                    make_normal_fast(S, pe[1], pe[2], T, Nm);
+                    normal(S, pe, Nm);
                     lambda *= 0.1f;
                 } else {
                     lambda *= 10.0f;
@@ -716,66 +783,76 @@ void* init_ptr(int npad)
     }
 }
 
-template <int G, int PPL, bool EXACT>
-static void* fit2_fn() { return reinterpret_cast<void*>(&fit2_kernel<G, PPL, EXACT>); }
+template <int G, int PPL, bool EXACT, int MODEL = 0>
+static void* fit2_fn() { return reinterpret_cast<void*>(&fit2_kernel<G, PPL, EXACT, MODEL>); }
 
 // Instantiated (G, PPL): exact fits for the workload geometries
 // (T = 21, 99 with G = 4; T = 201, 221 with G = 8; T = 21, 99, 201, 221 with
-// G = 16, 32) and a general ladder with full tail checks.
+// G = 16, 32) and a general ladder with full tail checks; model 1 (the Fano
+// lineshape) for the two- to eight-lane entries.
 struct Fit2Inst {
     int G, PPL;
     bool exact;
+    int model;
     void* (*fn)();
 };
 static const Fit2Inst kFit2[] = {
-    {2, 50, true, fit2_fn<2, 50, true>},   {2, 11, true, fit2_fn<2, 11, true>},
-    {4, 6, true, fit2_fn<4, 6, true>},     {4, 25, true, fit2_fn<4, 25, true>},
-    {8, 26, true, fit2_fn<8, 26, true>},   {8, 28, true, fit2_fn<8, 28, true>},
-    {8, 3, true, fit2_fn<8, 3, true>},     {8, 13, true, fit2_fn<8, 13, true>},
-    {16, 2, true, fit2_fn<16, 2, true>},   {16, 7, true, fit2_fn<16, 7, true>},
-    {16, 13, true, fit2_fn<16, 13, true>}, {16, 14, true, fit2_fn<16, 14, true>},
-    {32, 1, true, fit2_fn<32, 1, true>},   {32, 4, true, fit2_fn<32, 4, true>},
-    {32, 7, true, fit2_fn<32, 7, true>},
-    {4, 56, true, fit2_fn<4, 56, true>},   {4, 51, true, fit2_fn<4, 51, true>},
-    {2, 24, false, fit2_fn<2, 24, false>}, {2, 32, false, fit2_fn<2, 32, false>},
-    {2, 50, false, fit2_fn<2, 50, false>},
-    {4, 8, false, fit2_fn<4, 8, false>},   {4, 16, false, fit2_fn<4, 16, false>},
-    {4, 32, false, fit2_fn<4, 32, false>}, {8, 8, false, fit2_fn<8, 8, false>},
-    {8, 16, false, fit2_fn<8, 16, false>}, {8, 32, false, fit2_fn<8, 32, false>},
-    {16, 8, false, fit2_fn<16, 8, false>}, {16, 16, false, fit2_fn<16, 16, false>},
-    {32, 8, false, fit2_fn<32, 8, false>},
+    {2, 50, true, 0, fit2_fn<2, 50, true>},   {2, 11, true, 0, fit2_fn<2, 11, true>},
+    {4, 6, true, 0, fit2_fn<4, 6, true>},     {4, 25, true, 0, fit2_fn<4, 25, true>},
+    {8, 26, true, 0, fit2_fn<8, 26, true>},   {8, 28, true, 0, fit2_fn<8, 28, true>},
+    {8, 3, true, 0, fit2_fn<8, 3, true>},     {8, 13, true, 0, fit2_fn<8, 13, true>},
+    {16, 2, true, 0, fit2_fn<16, 2, true>},   {16, 7, true, 0, fit2_fn<16, 7, true>},
+    {16, 13, true, 0, fit2_fn<16, 13, true>}, {16, 14, true, 0, fit2_fn<16, 14, true>},
+    {32, 1, true, 0, fit2_fn<32, 1, true>},   {32, 4, true, 0, fit2_fn<32, 4, true>},
+    {32, 7, true, 0, fit2_fn<32, 7, true>},
+    {4, 56, true, 0, fit2_fn<4, 56, true>},   {4, 51, true, 0, fit2_fn<4, 51, true>},
+    {2, 24, false, 0, fit2_fn<2, 24, false>}, {2, 32, false, 0, fit2_fn<2, 32, false>},
+    {2, 50, false, 0, fit2_fn<2, 50, false>},
+    {4, 8, false, 0, fit2_fn<4, 8, false>},   {4, 16, false, 0, fit2_fn<4, 16, false>},
+    {4, 32, false, 0, fit2_fn<4, 32, false>}, {8, 8, false, 0, fit2_fn<8, 8, false>},
+    {8, 16, false, 0, fit2_fn<8, 16, false>}, {8, 32, false, 0, fit2_fn<8, 32, false>},
+    {16, 8, false, 0, fit2_fn<16, 8, false>}, {16, 16, false, 0, fit2_fn<16, 16, false>},
+    {32, 8, false, 0, fit2_fn<32, 8, false>},
+    // the Fano lineshape
+    {2, 50, true, 1, fit2_fn<2, 50, true, 1>},   {2, 11, true, 1, fit2_fn<2, 11, true, 1>},
+    {4, 6, true, 1, fit2_fn<4, 6, true, 1>},     {4, 25, true, 1, fit2_fn<4, 25, true, 1>},
+    {4, 56, true, 1, fit2_fn<4, 56, true, 1>},   {4, 51, true, 1, fit2_fn<4, 51, true, 1>},
+    {8, 26, true, 1, fit2_fn<8, 26, true, 1>},   {8, 28, true, 1, fit2_fn<8, 28, true, 1>},
+    {2, 24, false, 1, fit2_fn<2, 24, false, 1>}, {2, 32, false, 1, fit2_fn<2, 32, false, 1>},
+    {2, 50, false, 1, fit2_fn<2, 50, false, 1>}, {4, 32, false, 1, fit2_fn<4, 32, false, 1>},
+    {8, 32, false, 1, fit2_fn<8, 32, false, 1>},
 };
 
-void* fit2_ptr(int G, int PPL, bool exact)
+void* fit2_ptr(int G, int PPL, bool exact, int model)
 {
-    if (G == 1) return fit1_ptr();
+    if (G == 1) return model == 0 ? fit1_ptr() : nullptr;
     for (const Fit2Inst& f : kFit2)
-        if (f.G == G && f.PPL == PPL && f.exact == exact) return f.fn();
+        if (f.G == G && f.PPL == PPL && f.exact == exact && f.model == model) return f.fn();
     return nullptr;
 }
 
 // smallest instantiated PPL for (G, T); *exact tells whether it is ceil(T/G)
-int fit2_ppl(int G, int T, bool* exact)
+int fit2_ppl(int G, int T, bool* exact, int model)
 {
     if (G == 1) {   // the lane-per-frame kernel keeps spectra in shared memory
         *exact = true;
-        return T;
+        return model == 0 ? T : 0;
     }
     const int need = (T + G - 1) / G;
     for (const Fit2Inst& f : kFit2)
-        if (f.G == G && f.exact && f.PPL == need) {
+        if (f.G == G && f.exact && f.PPL == need && f.model == model) {
             *exact = true;
             return need;
         }
     int best = 0;
     for (const Fit2Inst& f : kFit2)
-        if (f.G == G && !f.exact && f.PPL >= need && (best == 0 || f.PPL < best)) best = f.PPL;
+        if (f.G == G && !f.exact && f.model == model && f.PPL >= need && (best == 0 || f.PPL < best)) best = f.PPL;
     *exact = false;
     return best;
 }
 
 int fit2_threads(int G) { return G == 1 ? 128 : 256; }
-size_t fit2_smem(int G, int T);
+size_t fit2_smem(int G, int T, int model);
 
 int init_npad(int n_outer)
 {
@@ -860,6 +937,21 @@ cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, i
     a.fb_count = fl.fb_count;
     a.iters_base = fl.iters_base;
     a.status_or = fl.status_or;
+    if (p->opts.model == CG_MODEL_FANO) {
+        // the Fano parameters on the fit's normalised abscissa u = (x - x_mid) / x_scale
+        const double g = p->opts.fano_gamma / p->x_scale;
+        a.fano_q = static_cast<float>(p->opts.fano_q);
+        a.fano_g = static_cast<float>(g);
+        a.fano_inv_g = static_cast<float>(1.0 / g);
+        a.fano_shift = static_cast<float>(p->opts.fano_q * g);
+        const double A0 = p->opts.fano_A, B0 = p->opts.fano_B, bx = p->opts.fano_box;
+        a.fano_A0 = static_cast<float>(A0);
+        a.fano_B0 = static_cast<float>(B0);
+        a.fano_Alo = static_cast<float>(std::min(A0 * (1.0 - bx), A0 * (1.0 + bx)));
+        a.fano_Ahi = static_cast<float>(std::max(A0 * (1.0 - bx), A0 * (1.0 + bx)));
+        a.fano_Blo = static_cast<float>(std::min(B0 * (1.0 - bx), B0 * (1.0 + bx)));
+        a.fano_Bhi = static_cast<float>(std::max(B0 * (1.0 - bx), B0 * (1.0 + bx)));
+    }
     a.row_stride = p->T | 1;
     a.counter = p->d.fit_counter;
     a.solve_f64 = p->solve_f64;
@@ -874,17 +966,17 @@ cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, i
     cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     void* args[] = {&a};
-    return cudaLaunchKernel(fit2_ptr(p->G2, p->PPL, p->ppl_exact), dim3(grid), dim3(threads), args,
-                            fit2_smem(p->G2, p->T), s);
+    return cudaLaunchKernel(fit2_ptr(p->G2, p->PPL, p->ppl_exact, p->opts.model), dim3(grid), dim3(threads), args,
+                            fit2_smem(p->G2, p->T, p->opts.model), s);
 }
 
-size_t fit2_smem(int G, int T)
+size_t fit2_smem(int G, int T, int model)
 {
     // G == 1: abscissa table, 4 warps x [2][32] row slots, 4 x 32 slot offsets;
     // G > 1: abscissa and 1 / reference tables, one PPL prefetch slot per thread
     if (G == 1) return sizeof(float) * (T + 4 * 64 * (T | 1)) + sizeof(int) * 4 * 32;
     bool exact = false;
-    const int ppl = fit2_ppl(G, T, &exact);
+    const int ppl = fit2_ppl(G, T, &exact, model);
     return sizeof(float) * (2 * T + (G >= 2 ? static_cast<size_t>(fit2_threads(G)) * (ppl | 1) : 0));
 }
 

@@ -269,6 +269,84 @@ __device__ __forceinline__ void make_normal_fast(const LmSums& S, float g, float
     N.b[3] = S.v[12];
 }
 
+// ---------------------------------------------------------------------------
+// The paper's Fano lineshape (c free; A, B boxed; q, gamma fixed):
+//   e = (u - c) / gamma, F = (q + e)^2 / (1 + e^2), m = B + A F
+//   dm/dc = -A F'(e) / gamma, F'(e) = 2 (q + e)(1 - q e) / (1 + e^2)^2,
+//   dm/dA = F, dm/dB = 1.
+// Sums: v0 jc jc, v1 jc F, v2 jc, v3 F F, v4 F, v5 jc r, v6 F r, v7 r,
+// v13 r r (the 1.1 entry is the point count).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void accum_point_fano(float u, float y, float c, float inv_g, float q, float A, float B,
+                                                 LmSums& S)
+{
+    const float e = (u - c) * inv_g;
+    const float id = rcp_fast(fmaf(e, e, 1.0f));
+    const float qe = q + e;
+    const float F = qe * qe * id;
+    const float r = fmaf(-A, F, y - B);
+    const float jc = -2.0f * A * inv_g * qe * fmaf(-q, e, 1.0f) * id * id;
+    S.v[0] = fmaf(jc, jc, S.v[0]);
+    S.v[1] = fmaf(jc, F, S.v[1]);
+    S.v[2] += jc;
+    S.v[3] = fmaf(F, F, S.v[3]);
+    S.v[4] += F;
+    S.v[5] = fmaf(jc, r, S.v[5]);
+    S.v[6] = fmaf(F, r, S.v[6]);
+    S.v[7] += r;
+    S.v[13] = fmaf(r, r, S.v[13]);
+}
+
+// Normal equations of (c, A, B) in H[0..5] = cc cA cB AA AB BB, b[0..2].
+__device__ __forceinline__ void make_normal_fano(const LmSums& S, int T, Normal& N)
+{
+    N.H[0] = S.v[0];
+    N.H[1] = S.v[1];
+    N.H[2] = S.v[2];
+    N.H[3] = S.v[3];
+    N.H[4] = S.v[4];
+    N.H[5] = static_cast<float>(T);
+    N.b[0] = S.v[5];
+    N.b[1] = S.v[6];
+    N.b[2] = S.v[7];
+}
+
+// (H + lambda diag H) delta = b for the 3 Fano parameters: Jacobi-scaled
+// Cholesky in R (float or double); false when not positive definite.  Bit 1
+// (A) or 2 (B) of held keeps that parameter's delta at zero and decouples it
+// from the others (the reduced system of an active bound).
+template <class R>
+__device__ __forceinline__ bool lm_solve3(const Normal& N, float lambda, int held, float (&delta)[3])
+{
+    const R h00 = N.H[0], h01 = N.H[1], h02 = N.H[2], h11 = N.H[3], h12 = N.H[4], h22 = N.H[5];
+    if (!(h00 > R(0)) || !(h11 > R(0)) || !(h22 > R(0)) || !(h00 < R(INFINITY)) || !(h11 < R(INFINITY)))
+        return false;
+    const R s0 = R(1) / sqrt(h00), s1 = R(1) / sqrt(h11), s2 = R(1) / sqrt(h22);
+    const R dg = R(1) + R(lambda);
+    const bool hA = (held & 2) != 0, hB = (held & 4) != 0;
+    const R m10 = hA ? R(0) : h01 * s1 * s0, m20 = hB ? R(0) : h02 * s2 * s0;
+    const R m21 = (hA || hB) ? R(0) : h12 * s2 * s1;
+    const R l00 = sqrt(dg);
+    const R l10 = m10 / l00, l20 = m20 / l00;
+    const R v11 = dg - l10 * l10;
+    if (!(v11 > R(0))) return false;
+    const R l11 = sqrt(v11);
+    const R l21 = (m21 - l20 * l10) / l11;
+    const R v22 = dg - l20 * l20 - l21 * l21;
+    if (!(v22 > R(0))) return false;
+    const R l22 = sqrt(v22);
+    const R z0 = R(N.b[0]) * s0 / l00;
+    const R z1 = ((hA ? R(0) : R(N.b[1]) * s1) - l10 * z0) / l11;
+    const R z2 = ((hB ? R(0) : R(N.b[2]) * s2) - l20 * z0 - l21 * z1) / l22;
+    const R u2 = z2 / l22;
+    const R u1 = (z1 - l21 * u2) / l11;
+    const R u0 = (z0 - l10 * u1 - l20 * u2) / l00;
+    delta[0] = static_cast<float>(u0 * s0);
+    delta[1] = static_cast<float>(u1 * s1);
+    delta[2] = static_cast<float>(u2 * s2);
+    return true;
+}
+
 // Cholesky of S H S + lambda I keeping only the inverse pivots (rsqrt).
 __device__ __forceinline__ bool lm_solve4_fast(const Normal& N, float lambda, float (&delta)[4])
 {

@@ -108,6 +108,11 @@ struct Fit2Args {
     int* fb_count;
     int iters_base;          // added to the reported iteration count
     int status_or;           // OR-ed into the reported status
+    // the Fano lineshape (model 1), on the normalised abscissa: asymmetry q,
+    // width g (fixed), the lowest-tooth shift q g, the boxes of A and B and
+    // their averages (the starting values)
+    float fano_q, fano_g, fano_inv_g, fano_shift;
+    float fano_A0, fano_B0, fano_Alo, fano_Ahi, fano_Blo, fano_Bhi;
 };
 
 // Arguments of the learned initial-guess inference kernel (cg_mlp_tc.cu).
@@ -289,11 +294,11 @@ FitArgs make_fit_args(const cg_plan_s* p);
 void* fast_readout_ptr(int Q, int sample_bytes = 2);
 void* init_ptr(int npad);
 int init_npad(int n_outer);
-void* fit2_ptr(int G, int PPL, bool exact);
-int fit2_ppl(int G, int T, bool* exact);
+void* fit2_ptr(int G, int PPL, bool exact, int model);
+int fit2_ppl(int G, int T, bool* exact, int model);
 int fit2_threads(int G);
 void* fit1_ptr();   // lane-per-frame LM kernel (cg_fit1.cu)
-size_t fit2_smem(int G, int T);
+size_t fit2_smem(int G, int T, int model);
 cudaError_t launch_fast_readout_i8(const cg_plan_s* p, const int8_t* frames, int64_t n, float* amps, float* y,
                                    cudaStream_t s);
 cudaError_t launch_fast_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps,

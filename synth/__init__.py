@@ -108,23 +108,30 @@ def _cycles(f_hz: np.ndarray, num: np.ndarray, fs: float) -> np.ndarray:
 
 
 def lineshape(x: np.ndarray, c: np.ndarray, fwhm: np.ndarray | float,
-              depth: np.ndarray | float = 0.7, shape: str = "dip") -> np.ndarray:
-    """Cavity transmission factor per tooth, shape [n_frames, T]."""
+              depth: np.ndarray | float = 0.7, shape: str = "dip", fano_q: float = 0.0) -> np.ndarray:
+    """Cavity transmission factor per tooth, shape [n_frames, T].  "dip" and
+    "peak" are Lorentzian; "fano" is the asymmetric profile
+    (1 - depth) + depth (q + e)^2 / (1 + e^2), e = (x - c) / (fwhm / 2), whose
+    baseline is 1 and whose q = 0 case is the dip."""
     g = np.asarray(fwhm, dtype=np.float64)[..., None] / 2.0 if np.ndim(fwhm) else fwhm / 2.0
     d = x[None, :] - np.asarray(c, dtype=np.float64)[:, None]
-    lor = (g * g) / (d * d + g * g)
-    if shape == "peak":
-        return lor
     dep = np.asarray(depth, dtype=np.float64)
     if dep.ndim:
         dep = dep[:, None]
+    if shape == "fano":
+        e = d / g
+        return (1.0 - dep) + dep * (fano_q + e) ** 2 / (1.0 + e * e)
+    lor = (g * g) / (d * d + g * g)
+    if shape == "peak":
+        return lor
     return 1.0 - dep * lor
 
 
 def frames(stream: Stream, n_frames: int, *, first_frame: int = 0, cavity: bool = True,
            center_amp_hz: float = 5e6, drive_hz: float = DRIVE_HZ, fwhm_hz=FWHM_HZ,
-           depth: float = 0.7, shape: str = "dip", sigma=None,
-           snr_db=None, noise_stream: int = 0, centers=None, device=None, bits: int = 12) -> dict:
+           depth=0.7, shape: str = "dip", sigma=None,
+           snr_db=None, noise_stream: int = 0, centers=None, device=None, bits: int = 12,
+           fano_q: float = 0.0) -> dict:
     """Synthesise ``n_frames`` int16 frames [n_frames, N] (see the module recipe).
 
     ``centers`` (per frame, Hz) replaces the sinusoidal drive; ``fwhm_hz``,
@@ -150,7 +157,7 @@ def frames(stream: Stream, n_frames: int, *, first_frame: int = 0, cavity: bool 
         centers = center_amp_hz * np.sin(2.0 * math.pi * drive_hz * t0)
     centers = np.asarray(centers, dtype=np.float64)
     if cavity:
-        shape_f = lineshape(g.tooth_x, centers, fwhm_hz, depth, shape)
+        shape_f = lineshape(g.tooth_x, centers, fwhm_hz, depth, shape, fano_q)
     else:
         shape_f = np.ones((n_frames, T))
     amp = E * stream.envelope[None, :] * shape_f                    # [n, T]

@@ -123,3 +123,27 @@ def test_plan_rejects_bad_learned_options(kw):
     with pytest.raises(cg.CgError) as ei:
         cg.cg_plan(1e9, 1000, np.array([11e6, 21e6, 31e6, 41e6, 51e6]), None, None, opts)
     assert ei.value.status == 1
+
+
+def test_fano_defaults_and_layout():
+    o = cg.cg_opts_default()
+    assert (o.model, o.fano_box, o.fano_q, o.fano_gamma) == (cg.MODEL_LORENTZ, 0.1, 0.0, 0.0)
+    # the ctypes mirror has the C layout: five doubles after the int block
+    assert ctypes.sizeof(_binding.cg_opts) == 112
+    assert _binding.cg_opts.fano_q.offset == 72
+
+
+@pytest.mark.parametrize("kw,status,err", [
+    (dict(model=7), 1, "model"),
+    (dict(model=1, fano_gamma=0.0, fano_A=0.7), 1, "fano_gamma"),
+    (dict(model=1, fano_gamma=4e7, fano_A=0.0), 1, "fano_A"),
+    (dict(model=1, fano_gamma=4e7, fano_A=0.7, fano_box=1.5), 1, "fano_box"),
+    (dict(model=1, fano_gamma=4e7, fano_A=0.7, fano_B=float("nan")), 1, "fano_A"),
+    (dict(model=1, fano_gamma=4e7, fano_A=0.7, init=1), 8, "Fano"),
+])
+def test_plan_rejects_bad_fano_options(kw, status, err):
+    opts = cg.cg_opts_default(**kw)
+    with pytest.raises(cg.CgError) as ei:
+        cg.cg_plan(1e9, 1000, np.array([11e6, 21e6, 31e6, 41e6, 51e6]), None, None, opts)
+    assert ei.value.status == status
+    assert err in str(ei.value)
