@@ -75,6 +75,8 @@ def _load():
         "or_fano_fit_batch": (None, [P, i64, P, i32, f64, f64, f64, f64, f64, P, i32, f64, f64,
                                      P, P, P, P, P]),
         "or_fano_grid_fit": (None, [P, P, i32, f64, f64, P, i32, P, i32, P, i32, P, P]),
+        "or_median_filter7": (None, [P, i64, i32, P]),
+        "or_median_init": (i32, [P, i64, i32, P, f64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -309,3 +311,31 @@ def fano_grid_fit(y, x, q, gamma, cgrid, Agrid, Bgrid):
     _load().or_fano_grid_fit(_p(ya), _p(xa), xa.size, float(q), float(gamma), _p(cg_), cg_.size, _p(ag), ag.size,
                              _p(bg), bg.size, _p(p), ctypes.byref(chi2))
     return p, chi2.value
+
+
+# ---------------------------------------------------------------------------
+# The paper's initial centre: 7x7 median filter of the time x tooth image
+# ---------------------------------------------------------------------------
+def median_filter7(y) -> np.ndarray:
+    """7x7 median filter of the image y[n, T] (rows = frames in time order),
+    mirrored edges (index -1 -> 0, n -> n - 1)."""
+    ya = _f64(y)
+    n, T = ya.shape
+    out = np.empty((n, T))
+    _load().or_median_filter7(_p(ya), n, T, _p(out))
+    return out
+
+
+def median_init(y, x, shift=0.0) -> dict:
+    """Initial centres of the rows of y[n, T]: x at the lowest value of each
+    median-filtered row (first tooth on ties) plus shift.  Returns dict(c0,
+    kmin, filtered)."""
+    ya = _f64(y)
+    n, T = ya.shape
+    xa = _f64(x)
+    c0 = np.empty(n)
+    kmin = np.empty(n, dtype=np.int32)
+    filt = np.empty((n, T))
+    if _load().or_median_init(_p(ya), n, T, _p(xa), float(shift), _p(c0), _p(kmin), _p(filt)) != 0:
+        raise MemoryError
+    return dict(c0=c0, kmin=kmin, filtered=filt)

@@ -31,8 +31,10 @@
  *     the fit stops as converged when a trial changes chi^2 by no more than
  *     tol * chi^2 (the lower of the two points is kept).
  *   - initial guess: moments of the spectrum about a baseline taken as the
- *     median of the outer fifth of the teeth (the paper's own initial guess,
- *     a 7x7 median filter over the time x tooth image, is not implemented).
+ *     median of the outer fifth of the teeth; and the paper's own initial
+ *     centre (or_median_*): the batch of spectra as a time x tooth image,
+ *     a 7x7 median filter with mirrored edges, the lowest filtered value of
+ *     each row.
  *
  * The paper's own lineshape (a Fano profile with the centre free, scale and
  * offset boxed to +-10 % of averages, asymmetry and width fixed) is the
@@ -739,4 +741,73 @@ void or_fano_grid_fit(const double* y, const double* x, int T, double q, double 
             }
     free(m);
     *chi2_best = best;
+}
+
+/* ------------------------------------------------------------------ */
+/* The paper's initial centre ("Data Capture and Processing", initial- */
+/* value paragraph; Fig. 3c): the normalised spectra of a batch form   */
+/* an image y[i][k] (frame i in time order, tooth k); a 2-D median     */
+/* filter with a 7x7 footprint is applied, and the lowest value of     */
+/* each filtered row gives the initial centre x_k (+ shift; the Fano   */
+/* profile's minimum lies q gamma below its centre).                   */
+/* Readings: the image edges are mirrored without repeating the edge   */
+/* sample's neighbour -- index -1 maps to 0, -2 to 1, n to n-1 (the    */
+/* "reflect" convention, d c b a | a b c d | d c b a, repeated for     */
+/* images smaller than the footprint); the median of the 49 values is  */
+/* the 25th smallest; ties in the row minimum go to the lowest tooth.  */
+/* ------------------------------------------------------------------ */
+static int64_t mirror_index(int64_t i, int64_t n)
+{
+    const int64_t period = 2 * n;
+    int64_t j = i % period;
+    if (j < 0) j += period;
+    return j >= n ? period - 1 - j : j;
+}
+
+static double median49(double* v)
+{
+    for (int i = 1; i < 49; ++i) {          /* insertion sort */
+        const double t = v[i];
+        int j = i - 1;
+        while (j >= 0 && v[j] > t) {
+            v[j + 1] = v[j];
+            --j;
+        }
+        v[j + 1] = t;
+    }
+    return v[24];
+}
+
+void or_median_filter7(const double* y, int64_t n, int T, double* out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double v[49];
+        for (int k = 0; k < T; ++k) {
+            int m = 0;
+            for (int di = -3; di <= 3; ++di)
+                for (int dk = -3; dk <= 3; ++dk)
+                    v[m++] = y[mirror_index(i + di, n) * T + mirror_index(k + dk, T)];
+            out[i * T + k] = median49(v);
+        }
+    }
+}
+
+/* c0[i] = x[kmin[i]] + shift with kmin[i] the first tooth of the lowest
+ * filtered value of row i; filtered (n x T) may be NULL. */
+int or_median_init(const double* y, int64_t n, int T, const double* x, double shift, double* c0, int* kmin,
+                   double* filtered)
+{
+    double* f = filtered ? filtered : (double*)malloc(sizeof(double) * (size_t)n * (size_t)T);
+    if (!f) return -1;
+    or_median_filter7(y, n, T, f);
+    for (int64_t i = 0; i < n; ++i) {
+        int best = 0;
+        for (int k = 1; k < T; ++k)
+            if (f[i * T + k] < f[i * T + best]) best = k;
+        kmin[i] = best;
+        c0[i] = x[best] + shift;
+    }
+    if (!filtered) free(f);
+    return 0;
 }
