@@ -235,6 +235,9 @@ def kernel_rooflines(stage_ms, stage_launches, n, g, T, args, mean_iters, hbm, b
         elif st == "init":
             b = (4 * T + 16 + 2) * frames
             r.update(bound="hbm", achieved=b / per / 1e9, peak=hbm, unit="GB/s")
+        elif st == "median":
+            b = (4 * T + 4) * frames                  # y in, the centre out
+            r.update(bound="hbm", achieved=b / per / 1e9, peak=hbm, unit="GB/s")
         elif st == "mlp":
             f = 2.0 * (T * 256 + 256 * 256) * frames
             r.update(bound="tensor", achieved=f / per / 1e12, peak=bf16, unit="TFLOP/s")
@@ -308,7 +311,7 @@ def run_ours(args):
                    readout={"fft": cg.READOUT_FFT, "gemm": cg.READOUT_GEMM_SPLIT,
                             "fold": cg.READOUT_FOLD_GEMM}[args.readout],
                    sample_bits=args.sample_bits,
-                   init=(cg.INIT_MLP if args.init == "mlp" else cg.INIT_MOMENT),
+                   init={"moment": cg.INIT_MOMENT, "mlp": cg.INIT_MLP, "median": cg.INIT_MEDIAN}[args.init],
                    polish_iter=args.polish, **fano_opts(args))
     if args.init == "mlp":
         with open(MLP_BLOB, "rb") as f:
@@ -380,7 +383,7 @@ def run_ours(args):
                    "lanes_per_frame": plan.info["lanes_per_frame"],
                    "path": ["auto", "fused", "split", "pipeline"][plan.info["path"]],
                    "fft_len": plan.info["fft_len"], "readout": args.readout,
-                   "init": "lowest tooth" if args.workload == "fano" else args.init,
+                   "init": "lowest tooth" if (args.workload == "fano" and args.init == "moment") else args.init,
                    "model": "fano" if args.workload == "fano" else "lorentz",
                    "polish_iter": args.polish if args.init == "mlp" else None},
         "input_gbs": total_frames * sb * g.frame_len / (ms_step / 1e3) / 1e9,
@@ -623,7 +626,7 @@ def main():
                     help="fft: pruned transform on the CUDA cores; gemm: DFT-at-teeth product on the "
                          "tensor cores; fold: coset fold on the CUDA cores + DFT at the teeth on the "
                          "tensor cores")
-    ap.add_argument("--init", choices=["moment", "mlp"], default="moment",
+    ap.add_argument("--init", choices=["moment", "mlp", "median"], default="moment",
                     help="initial guess; mlp loads the trained network (221 teeth)")
     ap.add_argument("--polish", type=int, default=0, help="LM polish steps after the MLP guess (0: 2)")
     ap.add_argument("--sample-bits", type=int, default=12,

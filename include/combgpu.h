@@ -70,7 +70,17 @@ typedef enum cg_status {
    frames that are not 4-byte aligned are read out by the general transform. */
 enum { CG_READOUT_FFT = 0, CG_READOUT_GEMM_SPLIT = 1, CG_READOUT_FOLD_GEMM = 2 };
 enum { CG_FFT_AUTO = 0, CG_FFT_FULL = 1, CG_FFT_COSET = 2 };
-enum { CG_INIT_MOMENT = 0, CG_INIT_MLP = 1 };
+/* Initial guess.  MOMENT: moments of the spectrum (Lorentzian) or the
+   lowest tooth (Fano).  MLP: the learned network (Lorentzian only).  MEDIAN
+   (the paper's, "Data Capture and Processing"): the frames of one
+   cg_process / cg_fit call form a time x tooth image (teeth in plan order);
+   a 7x7 median filter with mirrored edges (index -1 -> 0, n -> n - 1) is
+   applied and the lowest filtered value of each row gives the centre (first
+   tooth on ties; plus q gamma for the Fano profile); the Lorentzian's other
+   parameters come from the moments.  A MEDIAN call is processed as one
+   chunk (chunk_frames is ignored), since every row's filter reads three
+   rows on either side. */
+enum { CG_INIT_MOMENT = 0, CG_INIT_MLP = 1, CG_INIT_MEDIAN = 2 };
 /* Fitted lineshape.  LORENTZ: m = B + A g^2 / ((x - c)^2 + g^2), all four
    parameters free.  FANO (the paper's fit, "Data Capture and Processing"):
    m = B + A (q + e)^2 / (1 + e^2), e = (x - c) / gamma, with the centre c
@@ -103,7 +113,7 @@ typedef struct cg_opts {
                              CG_READOUT_FOLD_GEMM */
     int fft;              /* CG_FFT_AUTO: coset-pruned transform when every tooth bin
                              lies in one residue pair +-r mod M (M | N), else full */
-    int init;             /* CG_INIT_MOMENT (default) */
+    int init;             /* CG_INIT_MOMENT (default), CG_INIT_MLP or CG_INIT_MEDIAN */
     int max_iter;         /* LM trial steps per frame; paper: 20 */
     double tol;           /* relative chi^2 change for convergence; paper: 1e-6 */
     double lambda0;       /* initial Marquardt damping; 1e-3 */
@@ -294,6 +304,7 @@ enum {
     CG_STAGE_FIT = 3,       /* LM (full, or the polish steps after the MLP) */
     CG_STAGE_FALLBACK = 4,  /* moment guess + full LM of frames the polish left */
     CG_STAGE_FUSED = 5,     /* single-kernel path */
+    CG_STAGE_MEDIAN = 6,    /* median-filter initial centre */
     CG_N_STAGES = 8
 };
 cg_status cg_timing_enable(cg_plan_t plan, int enable);

@@ -24,7 +24,7 @@ from ._binding import (RESULT_DTYPE, INJECT_FAIL_LAUNCH, INJECT_HOLD, INJECT_THR
                        cg_stream_destroy, cg_stream_flush, cg_stream_poll, cg_stream_push,
                        cg_stream_stats, cg_stream_window)
 from ._binding import (FFT_AUTO, FFT_COSET, FFT_FULL, FIT_CONVERGED, FIT_FALLBACK, FIT_INIT_FLAT,
-                       FIT_MAX_ITER, FIT_NONFINITE, FIT_SINGULAR, INIT_MLP, INIT_MOMENT,
+                       FIT_MAX_ITER, FIT_NONFINITE, FIT_SINGULAR, INIT_MEDIAN, INIT_MLP, INIT_MOMENT,
                        READOUT_FFT, READOUT_GEMM_SPLIT, READOUT_FOLD_GEMM, PATH_AUTO, PATH_FUSED, PATH_SPLIT,
                        PATH_PIPELINE, MODEL_LORENTZ, MODEL_FANO)
 

@@ -27,10 +27,10 @@ FIT_CONVERGED, FIT_MAX_ITER, FIT_SINGULAR, FIT_NONFINITE, FIT_INIT_FLAT = 0, 1, 
 FIT_FALLBACK = 0x20
 STAGE_READOUT, STAGE_INIT, STAGE_MLP, STAGE_FIT, STAGE_FALLBACK, STAGE_FUSED = 0, 1, 2, 3, 4, 5
 N_STAGES = 8
-STAGE_NAMES = {0: "readout", 1: "init", 2: "mlp", 3: "fit", 4: "fallback", 5: "fused"}
+STAGE_NAMES = {0: "readout", 1: "init", 2: "mlp", 3: "fit", 4: "fallback", 5: "fused", 6: "median"}
 READOUT_FFT, READOUT_GEMM_SPLIT, READOUT_FOLD_GEMM = 0, 1, 2
 FFT_AUTO, FFT_FULL, FFT_COSET = 0, 1, 2
-INIT_MOMENT, INIT_MLP = 0, 1
+INIT_MOMENT, INIT_MLP, INIT_MEDIAN = 0, 1, 2
 PATH_AUTO, PATH_FUSED, PATH_SPLIT, PATH_PIPELINE = 0, 1, 2, 3
 MODEL_LORENTZ, MODEL_FANO = 0, 1
 

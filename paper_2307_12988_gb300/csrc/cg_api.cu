@@ -127,6 +127,7 @@ void free_tables(cg::DevTables& d)
     cudaFree(d.mlp_tab);
     cudaFree(d.fb_list);
     cudaFree(d.fb_count);
+    cudaFree(d.median_cx);
     d = cg::DevTables{};
 }
 
@@ -415,7 +416,8 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         return fail(CG_ERR_ARG, "readout must be CG_READOUT_FFT, CG_READOUT_GEMM_SPLIT or CG_READOUT_FOLD_GEMM");
     if (o.sample_bits != 12 && o.sample_bits != 16) return fail(CG_ERR_ARG, "sample_bits must be 12 or 16");
     if (o.solve_f64 < -1 || o.solve_f64 > 1) return fail(CG_ERR_ARG, "solve_f64 must be -1, 0 or 1");
-    if (o.init != CG_INIT_MOMENT && o.init != CG_INIT_MLP) return fail(CG_ERR_ARG, "init must be CG_INIT_MOMENT or CG_INIT_MLP");
+    if (o.init != CG_INIT_MOMENT && o.init != CG_INIT_MLP && o.init != CG_INIT_MEDIAN)
+        return fail(CG_ERR_ARG, "init must be CG_INIT_MOMENT, CG_INIT_MLP or CG_INIT_MEDIAN");
     if (o.polish_iter < 0 || o.polish_iter > 32767) return fail(CG_ERR_ARG, "polish_iter outside [0, 32767]");
     if (o.polish_iter == 0) o.polish_iter = 2;
     if (o.model != CG_MODEL_LORENTZ && o.model != CG_MODEL_FANO)
@@ -425,8 +427,9 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         if (!(o.fano_A != 0.0) || !std::isfinite(o.fano_A) || !std::isfinite(o.fano_B) || !std::isfinite(o.fano_q))
             return fail(CG_ERR_ARG, "fano_A (nonzero), fano_B and fano_q must be finite");
         if (!(o.fano_box >= 0.0) || !(o.fano_box < 1.0)) return fail(CG_ERR_ARG, "fano_box must be in [0, 1)");
-        if (o.init != CG_INIT_MOMENT)
-            return fail(CG_ERR_UNSUPPORTED, "the Fano model makes its own initial guess (init must be CG_INIT_MOMENT)");
+        if (o.init == CG_INIT_MLP)
+            return fail(CG_ERR_UNSUPPORTED, "the Fano model takes the lowest-tooth or median-filter initial centre "
+                                            "(init CG_INIT_MOMENT or CG_INIT_MEDIAN)");
     }
     for (size_t i = 0; i < sizeof(o.reserved) / sizeof(o.reserved[0]); ++i)
         if (o.reserved[i] != 0) return fail(CG_ERR_ARG, "reserved option fields must be zero");
@@ -640,6 +643,21 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         free_plan(p);
         return fail(CG_ERR_UNSUPPORTED, "no Fano fit kernel for this n_teeth and lanes_per_frame");
     }
+    if (o.init == CG_INIT_MEDIAN) {
+        // the median-filter guess writes x_k + shift (the Fano profile's
+        // minimum lies q gamma below its centre)
+        const double shift = o.model == CG_MODEL_FANO ? o.fano_q * o.fano_gamma : 0.0;
+        std::vector<float> cx(T);
+        for (int k = 0; k < T; ++k) cx[k] = static_cast<float>(p->x[k] + shift);
+        if ((e = upload(&p->d.median_cx, cx)) != cudaSuccess || (e = cg::setup_median(p)) != cudaSuccess) {
+            free_plan(p);
+            return cuda_fail(e, "median-filter initial guess set-up");
+        }
+        if (!p->median_ok || !p->fit_ok) {
+            free_plan(p);
+            return fail(CG_ERR_UNSUPPORTED, "the median-filter initial guess needs the fit kernels");
+        }
+    }
     if (o.init == CG_INIT_MLP && (!p->fit_ok || T > 256)) {
         free_plan(p);
         return fail(CG_ERR_UNSUPPORTED, "the learned initial guess needs the fit kernels and n_teeth <= 256");
@@ -676,7 +694,7 @@ cg_status cg_plan_describe(cg_plan_t p, cg_plan_info* info, int* bins_host)
     info->n_collisions = p->n_collisions;
     info->path = (p->opts.path == CG_PATH_AUTO) ? (p->fit_ok ? CG_PATH_PIPELINE : CG_PATH_FUSED)
                : (p->opts.path == CG_PATH_PIPELINE && !p->fit_ok) ? CG_PATH_FUSED : p->opts.path;
-    if (p->opts.readout != CG_READOUT_FFT || p->opts.init == CG_INIT_MLP || p->opts.model == CG_MODEL_FANO)
+    if (p->opts.readout != CG_READOUT_FFT || p->opts.init != CG_INIT_MOMENT || p->opts.model == CG_MODEL_FANO)
         info->path = CG_PATH_PIPELINE;
     if (info->path == CG_PATH_PIPELINE) info->lanes_per_frame = p->G2;
     if (bins_host) std::memcpy(bins_host, p->bins.data(), sizeof(int) * p->T);
@@ -739,7 +757,8 @@ static cg_status process_impl(cg_plan_t p, const void* frames, int sbytes, int64
     if (path == CG_PATH_PIPELINE && !p->fit_ok) path = CG_PATH_FUSED;
     // tensor-core readouts or learned guess: readout, then guess and fit kernels
     const bool fano = p->opts.model == CG_MODEL_FANO;
-    if (p->opts.readout != CG_READOUT_FFT || mlp || sbytes == 1 || fano) path = CG_PATH_PIPELINE;
+    const bool median = p->opts.init == CG_INIT_MEDIAN;
+    if (p->opts.readout != CG_READOUT_FFT || mlp || sbytes == 1 || fano || median) path = CG_PATH_PIPELINE;
     const bool fast = !gemm && !fold && p->fast_ok && aligned4;
     const bool pow2 = !gemm && !fold && !fast && p->pow2_ok && aligned4;
     if (path == CG_PATH_PIPELINE) {
@@ -760,8 +779,10 @@ static cg_status process_impl(cg_plan_t p, const void* frames, int sbytes, int64
         e = cudaEventRecord(p->ev_fork, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_read, p->ev_fork, 0);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_fit, p->ev_fork, 0);
-        for (int64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += p->chunk) {
-            const int64_t m = (n - c0) < p->chunk ? (n - c0) : p->chunk;
+        // the median filter runs over the call's whole time x tooth image
+        const int64_t chunk = median ? n : p->chunk;
+        for (int64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += chunk) {
+            const int64_t m = (n - c0) < chunk ? (n - c0) : chunk;
             const int64_t T = p->T;
             const char* fb = static_cast<const char*>(frames) + c0 * p->N * sbytes;
             const int16_t* fc = reinterpret_cast<const int16_t*>(fb);
@@ -785,6 +806,9 @@ static cg_status process_impl(cg_plan_t p, const void* frames, int sbytes, int64
             else if (e == cudaSuccess && !fano)
                 e = timed(p, CG_STAGE_INIT, p->s_read,
                           [&] { return cg::launch_init(p, yc, ac, m, pc, sc, p->s_read, nullptr, nullptr); });
+            if (e == cudaSuccess && median)   // the centre of the guess from the filtered image
+                e = timed(p, CG_STAGE_MEDIAN, p->s_read,
+                          [&] { return cg::launch_median(p, yc, ac, m, pc, p->s_read); });
             if (e == cudaSuccess) e = cudaEventRecord(p->ev_read, p->s_read);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_fit, p->ev_read, 0);
             if (e == cudaSuccess && mlp) {
@@ -814,8 +838,11 @@ static cg_status process_impl(cg_plan_t p, const void* frames, int sbytes, int64
                         return cg::launch_fit2(p, yc, ac, m, pc, sc, pc, rc, ic, sc, p->s_fit, fb);
                     });
             } else if (e == cudaSuccess) {
+                // the Fano fit reads a given centre only from the median filter
+                const float* p0 = (fano && !median) ? nullptr : pc;
+                const int16_t* fl = fano ? nullptr : sc;
                 e = timed(p, CG_STAGE_FIT, p->s_fit,
-                          [&] { return cg::launch_fit2(p, yc, ac, m, pc, sc, pc, rc, ic, sc, p->s_fit); });
+                          [&] { return cg::launch_fit2(p, yc, ac, m, p0, fl, pc, rc, ic, sc, p->s_fit); });
             }
         }
         if (e == cudaSuccess) e = cudaEventRecord(p->ev_join_r, p->s_read);
@@ -893,12 +920,20 @@ cg_status cg_fit(cg_plan_t p, const float* y, int64_t n, const float* p0, float*
     if (n < 0) return fail(CG_ERR_ARG, "n < 0");
     if (n == 0) return CG_OK;
     if (!y || !params) return fail(CG_ERR_ARG, "y_dev and params_dev are required");
-    cudaError_t e;
-    if (p->opts.model == CG_MODEL_FANO)   // the Fano fit makes its own guess; p0 is not read
-        e = cg::launch_fit2(p, y, nullptr, n, nullptr, nullptr, params, rss, iters, status,
-                            static_cast<cudaStream_t>(stream));
-    else
-        e = cg::launch_fit(p, y, nullptr, n, p0, params, rss, iters, status, static_cast<cudaStream_t>(stream));
+    cudaError_t e = cudaSuccess;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool fano = p->opts.model == CG_MODEL_FANO;
+    if (p->opts.init == CG_INIT_MEDIAN && !p0) {
+        // guess in params (Lorentzian: moments, then the filtered centre), then the fit from it
+        if (!fano) e = cg::launch_init(p, y, nullptr, n, params, status, s, nullptr, nullptr);
+        if (e == cudaSuccess) e = cg::launch_median(p, y, nullptr, n, params, s);
+        if (e == cudaSuccess)
+            e = cg::launch_fit2(p, y, nullptr, n, params, fano ? nullptr : status, params, rss, iters, status, s);
+    } else if (fano) {   // the Fano fit makes its own guess; p0 is not read
+        e = cg::launch_fit2(p, y, nullptr, n, nullptr, nullptr, params, rss, iters, status, s);
+    } else {
+        e = cg::launch_fit(p, y, nullptr, n, p0, params, rss, iters, status, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "cg_fit launch");
     return CG_OK;
 }

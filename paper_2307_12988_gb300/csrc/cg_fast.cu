@@ -546,8 +546,9 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
         // p, flag, lambda and counters of a frame that starts now
         auto start_frame = [&]() {
             if constexpr (MODEL == 1) {
-                // lowest tooth of the group's frame (first on ties), then the
-                // profile's minimum (e = -q) moved onto the centre
+                // a given centre (the median-filter guess), else the lowest
+                // tooth of the group's frame (first on ties); the profile's
+                // minimum (e = -q) moved onto the centre
                 float best = INFINITY;
                 int bk = 0x7fffffff;
 #pragma unroll
@@ -568,7 +569,7 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 256, G == 1 ? 3 : 2) fit2_kerne
                         bk = ok2;
                     }
                 }
-                p[0] = (bk < T ? us[bk] : 0.f) + a.fano_shift;
+                p[0] = a.p0 ? (a.p0[fr * 4] - a.x_mid) * inv_scale : (bk < T ? us[bk] : 0.f) + a.fano_shift;
                 p[1] = a.fano_g;
                 p[2] = fminf(fmaxf(a.fano_A0, a.fano_Alo), a.fano_Ahi);
                 p[3] = fminf(fmaxf(a.fano_B0, a.fano_Blo), a.fano_Bhi);

@@ -177,6 +177,18 @@ struct FoldArgs {
     int sm_W, sm_A, sm_stage, sm_tw, sm_iref, sm_bar, sm_total;
 };
 
+// Arguments of the median-filter initial centre (cg_median.cu).
+struct MedianArgs {
+    const float* y;          // [n][T] or null (then amps x inv_ref)
+    const float* amps;       // [n][T]
+    const float* inv_ref;    // [T]
+    const float* cx;         // [T] x_k + shift, abscissa units
+    float* params;           // [n][4]: c0 into column 0
+    int64_t n;
+    int T, S, R;             // teeth, shared row stride ((T + 6) | 1), rows per block
+    int sm_key, sm_total;    // shared-memory layout
+};
+
 struct DevTables {
     void* gemm_W = nullptr;       // [2][rows][Kpad] FP16 twiddles (hi, lo)
     void* fold_W = nullptr;       // [2][ntile][Kpad] FP16 twiddles of the folded readout
@@ -200,6 +212,7 @@ struct DevTables {
     int* fb_list = nullptr;       // [fb_cap] frames left by the polish
     int* fb_count = nullptr;      // [1]
     int64_t fb_cap = 0;
+    float* median_cx = nullptr;   // [T] x_k + shift of the median-filter guess
 };
 
 }  // namespace cg
@@ -232,6 +245,9 @@ struct cg_plan_s {
     // split-precision GEMM readout
     CUtensorMap gemm_map{};
     int gemm_split_x = 1, gemm_smem = 0, gemm_ntiles = 0;
+    bool median_ok = false;  // median-filter initial centre configured
+    cg::MedianArgs med{};
+    int grid_median = 0;
     bool pow2_ok = false;    // power-of-two full-transform readout configured
     cg::ReadoutArgs pa{};
     int grid_pow2 = 0;
@@ -327,6 +343,9 @@ cudaError_t launch_mlp(const cg_plan_s* p, const float* y, const float* amps, in
                        int16_t* flags, cudaStream_t s);
 
 // power-of-two full-transform readout (cg_pow2.cu)
+cudaError_t setup_median(cg_plan_s* p);
+cudaError_t launch_median(const cg_plan_s* p, const float* y, const float* amps, int64_t n, float* params,
+                          cudaStream_t s);
 cudaError_t setup_pow2(cg_plan_s* p);
 cudaError_t launch_pow2_readout(const cg_plan_s* p, const int16_t* frames, int64_t n, float* amps, float* y,
                                 cudaStream_t s);
