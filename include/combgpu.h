@@ -554,6 +554,44 @@ const char* cg_last_error(void);
 /* CG_VERSION of the loaded library. */
 int cg_version(void);
 
+/*
+ * ---- Displacement PSD and mechanical resonance ---------------------------
+ * Paper, "Experimental Results" and Fig. 6: the series of fitted cavity
+ * positions is turned into a power spectral density for several averaging
+ * times, and the accelerometer's mechanical resonance frequency f0 and
+ * quality factor Q are fitted to it.
+ *
+ * cg_psd_create -- tables and scratch for Welch PSDs with segments of
+ *   seg_len samples (4096, 8192, 16384 or 32768) on the current device.
+ *   Errors: CG_ERR_ARG (seg_len), CG_ERR_NOMEM / CG_ERR_CUDA.
+ * cg_psd_welch -- one-sided density of the series x_dev[i * stride],
+ *   i < n (float, device memory; e.g. the centre column of cg_process's
+ *   params with stride 4): segments of seg_len samples advanced by seg_len/2
+ *   (only complete segments), segment mean removed, periodic Hann window
+ *   w_n = 1/2 - 1/2 cos(2 pi n / seg_len), mean |rfft|^2 over the segments,
+ *   doubled except at DC and seg_len/2, divided by fs sum w^2.  psd_dev:
+ *   double [seg_len/2 + 1] (device), bin k at k fs / seg_len.  *n_segments
+ *   (host, may be NULL) receives the number of segments.  Asynchronous on
+ *   cuda_stream.  Errors: CG_ERR_ARG (NULL pointers, stride < 1, fs <= 0,
+ *   n < seg_len).  The transform runs in FP32, the averages in FP64.
+ * cg_resonance_fit -- fits S(f) = A f0^4 / ((f0^2 - f^2)^2 + (f f0/Q)^2) + B
+ *   to ln psd over the bins k with f_lo <= k df <= f_hi (k >= 1; at least 8
+ *   bins), FP64 Levenberg-Marquardt (at most max_iter steps; converged when a
+ *   step changes chi^2 by no more than tol chi^2; tol 1e-12 is a fine
+ *   default), initial values from the band (largest bin, smallest bin, the
+ *   width at half height).  out_dev: double [12] (device) = f0, Q, A, B, their
+ *   standard errors (from diag(H^-1) chi^2 / (n - 4)), chi^2, steps, status
+ *   (0 converged, 1 step limit, 2 singular, 3 non-finite), bins used.
+ *   Asynchronous.  Errors: CG_ERR_ARG.
+ */
+typedef struct cg_psd_s* cg_psd_t;
+cg_status cg_psd_create(int seg_len, cg_psd_t* out);
+void cg_psd_destroy(cg_psd_t psd);
+cg_status cg_psd_welch(cg_psd_t psd, const float* x_dev, int64_t n, int64_t stride, double fs,
+                       double* psd_dev, int64_t* n_segments, void* cuda_stream);
+cg_status cg_resonance_fit(const double* psd_dev, int n_bins, double df, double f_lo, double f_hi,
+                           int max_iter, double tol, double* out_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

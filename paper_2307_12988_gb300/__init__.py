@@ -19,6 +19,7 @@ from ._binding import (cg_mlp_adam, cg_mlp_backward, cg_mlp_create, cg_mlp_destr
                        cg_mlp_get_params, cg_mlp_infer, cg_mlp_load, cg_mlp_param_count, cg_mlp_save,
                        cg_mlp_set_norm, cg_mlp_set_params, cg_mlp_train_epoch, cg_timing_collect,
                        cg_timing_enable)
+from ._binding import cg_psd_create, cg_psd_destroy, cg_psd_welch, cg_resonance_fit
 from ._binding import (RESULT_DTYPE, INJECT_FAIL_LAUNCH, INJECT_HOLD, INJECT_THROTTLE_S, cg_clock,
                        cg_server_create, cg_server_destroy, cg_server_inject, cg_stream_create,
                        cg_stream_destroy, cg_stream_flush, cg_stream_poll, cg_stream_push,
@@ -28,7 +29,7 @@ from ._binding import (FFT_AUTO, FFT_COSET, FFT_FULL, FIT_CONVERGED, FIT_FALLBAC
                        READOUT_FFT, READOUT_GEMM_SPLIT, READOUT_FOLD_GEMM, PATH_AUTO, PATH_FUSED, PATH_SPLIT,
                        PATH_PIPELINE, MODEL_LORENTZ, MODEL_FANO)
 
-__all__ = ["Plan", "Mlp", "Server", "Stream", "CgError", "load", "cg_plan", "cg_plan_destroy", "cg_plan_describe",
+__all__ = ["Plan", "Mlp", "Psd", "Server", "Stream", "CgError", "load", "cg_plan", "cg_plan_destroy", "cg_plan_describe",
            "cg_process", "cg_readout", "cg_fit", "cg_reference_accumulate",
            "cg_set_reference", "cg_opts_default", "cg_status_string", "cg_version"]
 
@@ -126,6 +127,50 @@ class Plan:
 
     def timing_collect(self) -> dict:
         return cg_timing_collect(self.handle)
+
+
+class Psd:
+    """Welch PSD of a device series and the mechanical-resonance fit
+    (``cg_psd_*``, ``cg_resonance_fit``)."""
+
+    def __init__(self, seg_len=32768):
+        self.seg_len = int(seg_len)
+        self.handle = cg_psd_create(self.seg_len)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cg_psd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def welch(self, x, fs, stride=1, n=None):
+        """One-sided density of x[::stride] (device float tensor) as a device
+        float64 tensor [seg_len/2 + 1], and the number of segments."""
+        import torch
+        n = (x.numel() + stride - 1) // stride if n is None else n
+        out = torch.empty(self.seg_len // 2 + 1, dtype=torch.float64, device=x.device)
+        k = cg_psd_welch(self.handle, x, n, stride, fs, out)
+        return out, k
+
+    @staticmethod
+    def resonance(psd, df, f_lo, f_hi, max_iter=200, tol=1e-12):
+        """(f0, Q, A, B, their standard errors, chi^2, steps, status, bins)
+        fitted to the device PSD tensor, as a host numpy array."""
+        import torch
+        out = torch.empty(12, dtype=torch.float64, device=psd.device)
+        cg_resonance_fit(psd, psd.numel(), df, f_lo, f_hi, max_iter, tol, out)
+        return out.cpu().numpy()
 
 
 class Mlp:

@@ -99,6 +99,12 @@ _SIGS = {
     "cg_readout": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     "cg_readout_i8": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     "cg_fit": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
+    "cg_psd_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P)]),
+    "cg_psd_destroy": (None, [_P]),
+    "cg_psd_welch": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, _P,
+                                    ctypes.POINTER(ctypes.c_int64), _P]),
+    "cg_resonance_fit": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_double, _P, _P]),
     "cg_reference_accumulate": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     "cg_reference_accumulate_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     "cg_check_device": (ctypes.c_int, [_P]),
@@ -269,6 +275,29 @@ def cg_readout_i8(plan: int, frames, n_frames: int, amps, y, stream=None) -> Non
 def cg_readout(plan: int, frames, n_frames: int, amps, y, stream=None) -> None:
     _check(load().cg_readout(plan, _ptr(frames), int(n_frames), _ptr(amps), _ptr(y),
                              _stream(stream)), "cg_readout")
+
+
+def cg_psd_create(seg_len: int) -> int:
+    h = _P()
+    _check(load().cg_psd_create(int(seg_len), ctypes.byref(h)), "cg_psd_create")
+    return h.value
+
+
+def cg_psd_destroy(h: int) -> None:
+    load().cg_psd_destroy(h)
+
+
+def cg_psd_welch(h: int, x, n: int, stride: int, fs: float, psd_out, stream=None) -> int:
+    k = ctypes.c_int64(0)
+    _check(load().cg_psd_welch(h, _ptr(x), int(n), int(stride), float(fs), _ptr(psd_out), ctypes.byref(k),
+                               _stream(stream)), "cg_psd_welch")
+    return int(k.value)
+
+
+def cg_resonance_fit(psd, n_bins: int, df: float, f_lo: float, f_hi: float, max_iter: int, tol: float, out,
+                     stream=None) -> None:
+    _check(load().cg_resonance_fit(_ptr(psd), int(n_bins), float(df), float(f_lo), float(f_hi), int(max_iter),
+                                   float(tol), _ptr(out), _stream(stream)), "cg_resonance_fit")
 
 
 def cg_fit(plan: int, y, n: int, p0, params, rss, iters, status, stream=None) -> None:

@@ -256,3 +256,23 @@ def tooth_domain_spectra(geom: Geometry, n: int, *, seed: int, center_range_hz=1
     im = shape_f * np.sin(phase) + sb * rng.standard_normal((n, T))
     y = np.sqrt(re * re + im * im)
     return dict(y=y, c=c, fwhm=fwhm, snr_db=snr)
+
+
+def oscillator_series(n: int, fs: float, f0: float, Q: float, rms: float, floor: float = 0.0,
+                      seed: int = 0) -> np.ndarray:
+    """A thermally driven mechanical resonator sampled at fs: the AR(2)
+    recursion x_i = 2 r cos(w_d) x_{i-1} - r^2 x_{i-2} + e_i of a damped
+    oscillator (r = exp(-pi f0 / (Q fs)), w_d = 2 pi f0 / fs sqrt(1 - 1/4Q^2))
+    driven by white noise, scaled to the given RMS, plus a white floor of
+    standard deviation ``floor``; float64 [n]."""
+    from scipy.signal import lfilter
+    rng = np.random.default_rng(seed)
+    r = math.exp(-math.pi * f0 / (Q * fs))
+    wd = 2.0 * math.pi * f0 / fs * math.sqrt(1.0 - 1.0 / (4.0 * Q * Q))
+    burn = int(20 * Q * fs / f0) + 16                 # let the recursion forget its zero start
+    e = rng.standard_normal(n + burn)
+    x = lfilter([1.0], [1.0, -2.0 * r * math.cos(wd), r * r], e)[burn:]
+    x *= rms / np.std(x)
+    if floor:
+        x += floor * rng.standard_normal(n)
+    return x

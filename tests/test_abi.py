@@ -147,3 +147,15 @@ def test_plan_rejects_bad_fano_options(kw, status, err):
         cg.cg_plan(1e9, 1000, np.array([11e6, 21e6, 31e6, 41e6, 51e6]), None, None, opts)
     assert ei.value.status == status
     assert err in str(ei.value)
+
+
+def test_psd_entry_points_reject_bad_arguments_before_cuda():
+    lib = cg.load()
+    h = ctypes.c_void_p()
+    for bad in (0, 1000, 2048, 65536, 32769):
+        assert lib.cg_psd_create(bad, ctypes.byref(h)) == 1
+    assert lib.cg_psd_create(32768, None) == 1
+    k = ctypes.c_int64(0)
+    assert lib.cg_psd_welch(None, None, 100000, 1, 1e6, None, ctypes.byref(k), None) == 1
+    assert lib.cg_resonance_fit(None, 100, 30.0, 1e3, 2e3, 100, 1e-12, None, None) == 1
+    lib.cg_psd_destroy(None)                                           # NULL is ignored
