@@ -655,7 +655,10 @@ def run_psd(args):
     ms = ev[0].elapsed_time(ev[1]) / args.steps
     res = out.cpu().numpy()
     value = n / (ms / 1e3)
-    achieved = 4.0 * n / (ms / 1e3) / 1e9                 # the series' bytes, once
+    L = M // 2
+    flops = K * 5.0 * L * math.log2(L)                    # the complex transform of every segment
+    achieved = flops / (ms / 1e3) / 1e12
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     # end to end: the series from pinned host memory, the PSD and fit back
     xh = x.cpu().pin_memory()
     torch.cuda.synchronize()
@@ -684,8 +687,11 @@ def run_psd(args):
                    "l2": f"input ({4 * n / 1e9:.2f} GB) larger than L2; no flush"},
         "resonance": {"f0_hz": res[0], "f0_sigma_hz": res[4], "Q": res[1], "Q_sigma": res[5],
                       "steps": int(res[9]), "status": int(res[10])},
-        "roofline": {"kernel": "psd_welch_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind},
+        "roofline": {"kernel": "psd_welch_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                     "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                     "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)"},
+        "input_gbs": 4.0 * n / (ms / 1e3) / 1e9,
+        "input_hbm_frac": 4.0 * n / (ms / 1e3) / 1e9 / hbm,
         "cpu_baseline": {"value": sample.size / cpu_s, "unit": "samples/s", "cores": 1, "kind": "oracle",
                          "sample": f"first {sample.size} samples (numpy FP64 Welch + LM fit), {cpu_s:.1f} s"},
         "e2e": {"value": n / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 4 * n,

@@ -8,9 +8,10 @@
 // segments, one-sided density (factor 2 except at DC and M/2) / (fs sum w^2).
 // psd_welch_kernel<L>: one segment per block pass, L/16 threads; the
 // segment's L packed complex values z_n = x_2n + i x_2n+1 stay in shared
-// memory through in-place Stockham stages of radix 16 (and one smaller
-// radix), each thread holding 16 values in registers between a stage's read
-// and write; the real-FFT split X_k = E_k + W_M^k O_k gives |X_k|^2 for
+// memory (one pad per 16 values against bank conflicts) through in-place
+// Stockham stages of radix 16 (and one smaller radix), each thread holding
+// 16 values in registers between a stage's read and write, twiddles of all
+// but a final small-radix stage from a shared table; the real-FFT split X_k = E_k + W_M^k O_k gives |X_k|^2 for
 // k = 0..L, which each thread accumulates in FP64 registers over all the
 // segments its block takes; per-block partials are summed and scaled by
 // psd_reduce_kernel.
@@ -56,14 +57,31 @@ struct PsdArgs {
     double* part;
 };
 
+// position of complex value i in the exchange buffer: one pad per 16 values,
+// so the first stage's 16-value-stride writes fall on distinct banks
+__device__ __forceinline__ int zp(int i) { return i + (i >> 4); }
+
+// twiddles: W_L^(q s) for q < min(L, 4096), s = max(1, L / 4096), in shared
+// memory (every stage but a last one of radix < 16 at L > 4096 indexes a
+// multiple of s); that last stage reads the full table from global memory
+template <int L>
+struct TwShared {
+    static constexpr int kStride = L > 4096 ? L / 4096 : 1;
+    static constexpr int kSize = L > 4096 ? 4096 : L;
+};
+
 template <int R>
 struct StageShape {
     static constexpr int kPerThread = 16 / R;   // butterflies per thread
 };
 
 // one in-place Stockham stage of radix R over the L values in z
-template <int L, int R>
-__device__ __forceinline__ void stage_inplace(float2* z, int Ns, const float2* __restrict__ twL)
+// twiddle source of a stage: 0 the global table, 1 the shared W_L^(q s)
+// table, 2 the shared W_256^q table (the Ns = 16 stage: consecutive frames
+// read consecutive entries instead of entries 16 apart)
+template <int L, int R, int kTw>
+__device__ __forceinline__ void stage_inplace(float2* z, int Ns, const float2* __restrict__ ts,
+                                              const float2* __restrict__ t256, const float2* __restrict__ twL)
 {
     constexpr int NT = L / 16, per = L / R, NB = StageShape<R>::kPerThread;
     const int t = threadIdx.x;
@@ -72,7 +90,7 @@ __device__ __forceinline__ void stage_inplace(float2* z, int Ns, const float2* _
     for (int b = 0; b < NB; ++b) {
         const int j = t + NT * b;
 #pragma unroll
-        for (int r = 0; r < R; ++r) a[b][r] = z[j + r * per];
+        for (int r = 0; r < R; ++r) a[b][r] = z[zp(j + r * per)];
     }
     __syncthreads();
     const int twstep = L / (Ns * R);
@@ -82,12 +100,18 @@ __device__ __forceinline__ void stage_inplace(float2* z, int Ns, const float2* _
         const int k = j & (Ns - 1);
         if (Ns > 1) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) a[b][r] = cmul(a[b][r], __ldg(&twL[r * k * twstep]));
+            for (int r = 1; r < R; ++r) {
+                const int m = r * k * twstep;
+                const float2 w = kTw == 2   ? t256[r * k]
+                                 : kTw == 1 ? ts[m / TwShared<L>::kStride]
+                                            : __ldg(&twL[m]);
+                a[b][r] = cmul(a[b][r], w);
+            }
         }
         Dft<R>::run(a[b]);
         const int idx = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) z[idx + r * Ns] = a[b][r];
+        for (int r = 0; r < R; ++r) z[zp(idx + r * Ns)] = a[b][r];
     }
     __syncthreads();
 }
@@ -96,9 +120,13 @@ template <int L>
 __global__ void __launch_bounds__(L / 16) psd_welch_kernel(PsdArgs a)
 {
     constexpr int NT = L / 16, M = 2 * L;
-    extern __shared__ __align__(16) float2 z[];   // [L]
+    extern __shared__ __align__(16) float2 z[];   // [L + L/16] (padded), then the twiddle table
+    float2* ts = z + L + L / 16;                  // [TwShared<L>::kSize]
+    float2* t256 = ts + TwShared<L>::kSize;       // [256] W_256^q
     __shared__ double red[NT / 32];
     const int t = threadIdx.x;
+    for (int i = t; i < TwShared<L>::kSize; i += NT) ts[i] = a.twL[i * TwShared<L>::kStride];
+    for (int i = t; i < 256; i += NT) t256[i] = a.twL[i * (L / 256)];
     // FP64 sums of |X_k|^2 in registers; at L = 16384 (1024 threads, 64
     // registers each) in the block's own L2-resident row of part instead
     constexpr bool kRowAcc = L == 16384;
@@ -132,18 +160,18 @@ __global__ void __launch_bounds__(L / 16) psd_welch_kernel(PsdArgs a)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const int n = t + NT * j;
-            z[n] = make_float2((v[j].x - mean) * __ldg(a.win + 2 * n), (v[j].y - mean) * __ldg(a.win + 2 * n + 1));
+            z[zp(n)] = make_float2((v[j].x - mean) * __ldg(a.win + 2 * n), (v[j].y - mean) * __ldg(a.win + 2 * n + 1));
         }
         __syncthreads();
         // L = 16^3 * Rl (Rl = 2, 4) or 16^2 * 8
-        stage_inplace<L, 16>(z, 1, a.twL);
-        stage_inplace<L, 16>(z, 16, a.twL);
+        stage_inplace<L, 16, 1>(z, 1, ts, t256, a.twL);
+        stage_inplace<L, 16, 2>(z, 16, ts, t256, a.twL);
         if constexpr (L == 2048) {
-            stage_inplace<L, 8>(z, 256, a.twL);
+            stage_inplace<L, 8, 1>(z, 256, ts, t256, a.twL);
         } else {
-            stage_inplace<L, 16>(z, 256, a.twL);
-            if constexpr (L == 8192) stage_inplace<L, 2>(z, 4096, a.twL);
-            if constexpr (L == 16384) stage_inplace<L, 4>(z, 4096, a.twL);
+            stage_inplace<L, 16, 1>(z, 256, ts, t256, a.twL);
+            if constexpr (L == 8192) stage_inplace<L, 2, 0>(z, 4096, ts, t256, a.twL);
+            if constexpr (L == 16384) stage_inplace<L, 4, 0>(z, 4096, ts, t256, a.twL);
         }
         // real-FFT split at every bin k = 0..L
 #pragma unroll
@@ -151,8 +179,8 @@ __global__ void __launch_bounds__(L / 16) psd_welch_kernel(PsdArgs a)
             const int k = t + NT * j;
             if (j < 16 || t == 0) {
                 const int kk = (j == 16) ? L : k;
-                const float2 Zb = z[kk & (L - 1)];
-                const float2 Zr = z[(L - kk) & (L - 1)];
+                const float2 Zb = z[zp(kk & (L - 1))];
+                const float2 Zr = z[zp((L - kk) & (L - 1))];
                 const float2 E = make_float2(0.5f * (Zb.x + Zr.x), 0.5f * (Zb.y - Zr.y));
                 const float2 Dd = make_float2(0.5f * (Zb.x - Zr.x), 0.5f * (Zb.y + Zr.y));
                 const float2 O = make_float2(Dd.y, -Dd.x);
@@ -504,7 +532,7 @@ cg_status cg_psd_create(int seg_len, cg_psd_t* out)
     }
     int sms = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    h->smem = sizeof(float2) * static_cast<size_t>(L);
+    h->smem = sizeof(float2) * (static_cast<size_t>(L) + L / 16 + (L > 4096 ? 4096 : L) + 256);
     if (e == cudaSuccess) e = cg::raise_smem_limit(fn, h->smem);
     int occ = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, L / 16, h->smem);
