@@ -18,13 +18,16 @@
 //      window's 7 column medians (at most 21 of the 49 values lie below the
 //      smallest column median, at most 21 above the largest); windows with
 //      L(k) <= min_k U(k) are candidates (about 12 of 99 at the paper rate);
-//   4. each candidate window's exact median: sort its 7 columns, then its 7
-//      rows (the matrix stays sorted both ways), drop the 10 elements with
-//      more than 25 elements above or below them by position, and select the
-//      15th smallest of the 29 left by forgetful selection (discard the
-//      minimum and maximum of a shrinking buffer); the row keeps the least
-//      (value, tooth) key by a 64-bit shared-memory atomicMin;
-//   5. c0 of each row into params[i][0].
+//   4. the exact median t of the window of least U (sort its 7 columns, then
+//      its 7 rows -- the matrix stays sorted both ways --, drop the 10
+//      elements with more than 25 elements above or below them by position,
+//      select the 15th smallest of the 29 left by forgetful selection);
+//   5. every candidate is compared with t by counting its values below and
+//      at or below t: a median below t (rare) is computed exactly and
+//      competes by a 64-bit (value, tooth) atomicMin, a median equal to t
+//      keeps its tooth by atomicMin; with no median below t, the first tooth
+//      whose median equals t is the row's minimum;
+//   6. c0 of each row into params[i][0].
 // Every selection moves values without arithmetic, so the result is an
 // element of the window, equal to the definition's.
 #include <cstdint>
@@ -144,6 +147,9 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
     int* list = reinterpret_cast<int*>(cm + R * S);                    // [R T]
     unsigned long long* key = reinterpret_cast<unsigned long long*>(msm + a.sm_key);   // [R]
     int* count = reinterpret_cast<int*>(key + R);
+    int* ka = count + 4;                                               // [R] first window of least U
+    float* tq = reinterpret_cast<float*>(ka + R);                      // [R] its exact median
+    int* tie = reinterpret_cast<int*>(tq + R);                         // [R] first window with median = tq
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kMedThreads / 32;
@@ -159,7 +165,10 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
                 tile[t * S + j] = a.y ? src[k] : __fmul_rn(src[k], a.inv_ref[k]);
             }
         }
-        if (tid < R) key[tid] = ~0ull;
+        if (tid < R) {
+            key[tid] = ~0ull;
+            tie[tid] = 0x7fffffff;
+        }
         if (tid == 0) *count = 0;
         __syncthreads();
         // 2. medians of the 7-row column segments
@@ -176,14 +185,26 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
         for (int r = warp; r < rows; r += kWarps) {
             const float* cr = cm + r * S;
             float ustar = INFINITY;
+            int kbest = 0x7fffffff;
             for (int k = lane; k < T; k += 32) {
                 float hi = cr[k];
 #pragma unroll
                 for (int d = 1; d < 7; ++d) hi = fmaxf(hi, cr[k + d]);
-                ustar = fminf(ustar, hi);
+                if (hi < ustar) {
+                    ustar = hi;
+                    kbest = k;
+                }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) ustar = fminf(ustar, __shfl_xor_sync(0xffffffffu, ustar, o));
+            for (int o = 16; o > 0; o >>= 1) {
+                const float uo = __shfl_xor_sync(0xffffffffu, ustar, o);
+                const int ko = __shfl_xor_sync(0xffffffffu, kbest, o);
+                if (uo < ustar || (uo == ustar && ko < kbest)) {
+                    ustar = uo;
+                    kbest = ko;
+                }
+            }
+            if (lane == 0) ka[r] = kbest < T ? kbest : 0;
             for (int k0 = 0; k0 < T; k0 += 32) {
                 const int k = k0 + lane;
                 bool cand = false;
@@ -201,19 +222,41 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
             }
         }
         __syncthreads();
-        // 4. exact medians of the candidate windows
+        // 4. the exact median t of each row's window of least U (an upper
+        //    bound of the row minimum)
+        if (tid < rows) tq[tid] = window_median(tile, S, tid, ka[tid]);
+        __syncthreads();
+        // 5. each candidate against t by counting: 25 or more values below t
+        //    means a median below t (its exact median then competes by the
+        //    (value, tooth) key); otherwise 25 or more values at or below t
+        //    means a median equal to t (the first such tooth is kept).  With
+        //    no median below t the minimum is t itself.
         const int nc = *count;
         for (int e = tid; e < nc; e += kMedThreads) {
             const int it = list[e];
             const int r = it >> 16, k = it & 0xffff;
-            const float med = window_median(tile, S, r, k);
-            const unsigned long long kv = (static_cast<unsigned long long>(ord(med)) << 32) | static_cast<unsigned>(k);
-            atomicMin(&key[r], kv);
+            const float t = tq[r];
+            int lt = 0, le = 0;
+#pragma unroll
+            for (int c = 0; c < 7; ++c)
+#pragma unroll
+                for (int j = 0; j < 7; ++j) {
+                    const float v = tile[(r + j) * S + k + c];
+                    lt += v < t ? 1 : 0;
+                    le += v <= t ? 1 : 0;
+                }
+            if (lt >= 25) {
+                const float med = window_median(tile, S, r, k);
+                atomicMin(&key[r], (static_cast<unsigned long long>(ord(med)) << 32) | static_cast<unsigned>(k));
+            } else if (le >= 25) {
+                atomicMin(&tie[r], k);
+            }
         }
         __syncthreads();
-        // 5. the initial centres
+        // 6. the initial centres
         if (tid < rows) {
-            const unsigned kk = static_cast<unsigned>(key[tid] & 0xffffffffull);
+            const unsigned long long kv = key[tid];
+            const unsigned kk = kv != ~0ull ? static_cast<unsigned>(kv & 0xffffffffull) : static_cast<unsigned>(tie[tid]);
             const int k = kk < static_cast<unsigned>(T) ? static_cast<int>(kk) : 0;
             a.params[(i0 + tid) * 4] = a.cx[k];
         }
@@ -238,7 +281,7 @@ cudaError_t setup_median(cg_plan_s* p)
     auto bytes = [&](int r) {
         const size_t tables = sizeof(float) * (static_cast<size_t>(r + 6) * S + static_cast<size_t>(r) * S) +
                               sizeof(int) * static_cast<size_t>(r) * T;
-        return ((tables + 15) & ~static_cast<size_t>(15)) + 8 * r + 16;
+        return ((tables + 15) & ~static_cast<size_t>(15)) + 8 * r + 16 + 12 * r;
     };
     while (R > 4 && bytes(R) > 100 * 1024) R /= 2;
     m.R = R;
