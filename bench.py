@@ -138,13 +138,20 @@ GEOMETRIES = {
     # the paper's fitted lineshape: Fano profile (q = 0.3, FWHM 80 MHz, depth 0.7)
     # at the paper rate, fitted with the centre free, scale and offset boxed
     "fano": ("PAPER_RATE", dict(snr_db=30.0, center_amp_hz=20e6, shape="fano", fano_q=FANO_Q)),
+    # the paper's whole configuration: its 8-bit 2.2 GS/s digitiser frames and
+    # its Fano fit (with --init median, its initial centre too)
+    "fano8": ("PAPER_8BIT", dict(snr_db=30.0, center_amp_hz=20e6, bits=8, shape="fano", fano_q=FANO_Q)),
 }
+
+
+def is_fano(args) -> bool:
+    return args.workload in ("fano", "fano8")
 
 
 def fano_opts(args) -> dict:
     """Plan options of the Fano workload: q and gamma fixed at the generator's
     values, scale and offset boxed +-10 % around the lineshape's 0.7 / 0.3."""
-    if args.workload != "fano":
+    if not is_fano(args):
         return {}
     import paper_2307_12988_gb300 as cg
     return dict(model=cg.MODEL_FANO, fano_q=FANO_Q, fano_gamma=FWHM_HZ / 2.0, fano_A=0.7, fano_B=0.3,
@@ -158,7 +165,7 @@ FIT_DESC = {False: "moment init, 20-iteration LM",
 def oracle_fit(y, x, args, converged=False):
     """The oracle's fit of the workload's model on spectra y."""
     import oracle
-    if args.workload == "fano":
+    if is_fano(args):
         r = oracle.fano_fit_batch(y, x, FANO_Q, FWHM_HZ / 2.0, 0.7, 0.3, box=0.1, converged=converged)
         return dict(r, params=np.column_stack([r["params"][:, 0], np.full(len(y), FWHM_HZ / 2.0),
                                                r["params"][:, 1:]]))
@@ -168,7 +175,7 @@ def oracle_fit(y, x, args, converged=False):
 def oracle_process(frames, bins, ref, x, args):
     """The oracle's whole path (readout, initial guess, LM) for the workload."""
     import oracle
-    if args.workload == "fano":
+    if is_fano(args):
         _, y = oracle.readout(frames, bins, ref)
         return oracle_fit(y, x, args)
     return oracle.process(frames, bins, ref, x)
@@ -242,7 +249,7 @@ def kernel_rooflines(stage_ms, stage_launches, n, g, T, args, mean_iters, hbm, b
             f = 2.0 * (T * 256 + 256 * 256) * frames
             r.update(bound="tensor", achieved=f / per / 1e12, peak=bf16, unit="TFLOP/s")
         elif st == "fit":
-            fp = LM_FLOP_PER_POINT_FANO if args.workload == "fano" else LM_FLOP_PER_POINT
+            fp = LM_FLOP_PER_POINT_FANO if is_fano(args) else LM_FLOP_PER_POINT
             f = fp * T * (mean_iters + 1.0) * frames
             r.update(bound="alu", achieved=f / per / 1e12, peak=alu_peak, unit="TFLOP/s")
         if "achieved" in r:
@@ -272,7 +279,7 @@ def cpu_baseline_leg(frames, params, status, iters, plan, ref, g, args) -> dict:
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     cpu = {"value": n / dt, "unit": "spectra/s", "cores": cores, "kind": "oracle",
            "sample": f"first {n} of the workload's frames (FP64 direct-sum DFT at the "
-                     f"{g.n_teeth} teeth, {FIT_DESC[args.workload == 'fano']}), {dt:.1f} s"}
+                     f"{g.n_teeth} teeth, {FIT_DESC[is_fano(args)]}), {dt:.1f} s"}
     rng = np.random.default_rng(7)
     idx = np.sort(rng.choice(frames_host.shape[0], size=min(256, frames_host.shape[0]),
                              replace=False))
@@ -383,8 +390,8 @@ def run_ours(args):
                    "lanes_per_frame": plan.info["lanes_per_frame"],
                    "path": ["auto", "fused", "split", "pipeline"][plan.info["path"]],
                    "fft_len": plan.info["fft_len"], "readout": args.readout,
-                   "init": "lowest tooth" if (args.workload == "fano" and args.init == "moment") else args.init,
-                   "model": "fano" if args.workload == "fano" else "lorentz",
+                   "init": "lowest tooth" if (is_fano(args) and args.init == "moment") else args.init,
+                   "model": "fano" if is_fano(args) else "lorentz",
                    "polish_iter": args.polish if args.init == "mlp" else None},
         "input_gbs": total_frames * sb * g.frame_len / (ms_step / 1e3) / 1e9,
         "roofline": {"kernel": dominant, "bound": dom.get("bound"), "achieved": dom.get("achieved"),

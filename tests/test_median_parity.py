@@ -134,3 +134,24 @@ def test_lorentzian_fit_from_the_median_guess(dev):
     dc = np.abs(o["params"][ok, 0] - full["params"][ok, 0])
     print(f"\n[median + lorentz] centre err max {dc.max():.1f} Hz, mean iters {o['iters'].mean():.2f}")
     assert np.all(dc <= CENTER_TOL)
+
+
+def test_the_papers_configuration_on_8bit_frames(dev):
+    # 8-bit samples at 2.2 GS/s in 2200-sample frames, the median-filter
+    # centre and the boxed Fano fit: the paper's whole processing chain
+    g = synth.PAPER_8BIT
+    q = 0.3
+    stream = synth.make_stream(g, synth.BASE_SEED + 740)
+    frames = synth.frames(stream, 2000, snr_db=30.0, center_amp_hz=20e6, shape="fano", fano_q=q, bits=8)["frames"]
+    rf = synth.frames(stream, 1000, cavity=False, noise_stream=1, snr_db=30.0, bits=8)["frames"]
+    bins = oracle.tooth_bins(g.sample_rate, g.frame_len, g.tooth_freqs)
+    ref = oracle.reference(rf, bins)
+    y = oracle.readout(frames, bins, ref)[1]
+    assert frames.dtype == np.int8
+    o = _process(dev, g, frames, ref, **_fano_opts(q))
+    rf_ = oracle.fano_fit_batch(y, g.tooth_x, q, GAMMA, 0.7, 0.3, box=0.1, converged=True)
+    ok = ((o["status"] & 3) == 0) & (rf_["status"] == 0)
+    assert ok.mean() >= 0.99
+    dc = np.abs(o["params"][ok, 0] - rf_["params"][ok, 0])
+    print(f"\n[8-bit + median + fano] centre err max {dc.max():.1f} Hz, mean iters {o['iters'].mean():.2f}")
+    assert np.all(dc <= CENTER_TOL)
