@@ -13,7 +13,7 @@
 // exactly only where the minimum can be.  Per block, R consecutive rows:
 //   1. the (R + 6) x (T + 6) tile of y (mirrored rows and teeth) goes to
 //      shared memory, so that no window needs an index mapping;
-//   2. the median of each 7-row column segment (a 16-comparator network);
+//   2. the median of each 7-row column segment (a pruned sorting network);
 //   3. per row, bounds of each window's median: L(k) = min, U(k) = max of the
 //      window's 7 column medians (at most 21 of the 49 values lie below the
 //      smallest column median, at most 21 above the largest); windows with
@@ -40,6 +40,7 @@ namespace cg {
 namespace {
 
 constexpr int kMedThreads = 256;
+constexpr int kMaxKPerLane = 16;   // windows per lane in the bounds pass: T <= 512
 
 __device__ __forceinline__ void cmpx(float& a, float& b)
 {
@@ -58,6 +59,19 @@ __device__ __forceinline__ void sort7(float (&v)[7])
     cmpx(v[1], v[2]); cmpx(v[4], v[6]);
     cmpx(v[2], v[3]); cmpx(v[4], v[5]);
     cmpx(v[1], v[2]); cmpx(v[3], v[4]); cmpx(v[5], v[6]);
+}
+
+// median of 7 values: the sorting network above pruned to the comparators
+// that reach the middle output, each keeping only the outputs used later
+// (22 min/max operations instead of 32; checked on the 128 binary inputs)
+__device__ __forceinline__ float median7(float (&v)[7])
+{
+    cmpx(v[0], v[6]); cmpx(v[2], v[3]); cmpx(v[4], v[5]);
+    cmpx(v[0], v[2]); cmpx(v[1], v[4]); cmpx(v[3], v[6]);
+    v[1] = fmaxf(v[0], v[1]); cmpx(v[2], v[5]); cmpx(v[3], v[4]);
+    v[2] = fmaxf(v[1], v[2]); v[4] = fminf(v[4], v[6]);
+    v[3] = fmaxf(v[2], v[3]); v[4] = fminf(v[4], v[5]);
+    return fminf(v[3], v[4]);
 }
 
 // median of N = 2M + 1 values by forgetful selection: the buffer v[t .. M+2)
@@ -177,8 +191,7 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
                 float v[7];
 #pragma unroll
                 for (int q = 0; q < 7; ++q) v[q] = tile[(r + q) * S + j];
-                sort7(v);
-                cm[r * S + j] = v[3];
+                cm[r * S + j] = median7(v);
             }
         __syncthreads();
         // 3. per row (one warp): bounds and the candidate windows
@@ -186,13 +199,23 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
             const float* cr = cm + r * S;
             float ustar = INFINITY;
             int kbest = 0x7fffffff;
-            for (int k = lane; k < T; k += 32) {
-                float hi = cr[k];
+            float lo[kMaxKPerLane];                // L(k) of this lane's windows
 #pragma unroll
-                for (int d = 1; d < 7; ++d) hi = fmaxf(hi, cr[k + d]);
-                if (hi < ustar) {
-                    ustar = hi;
-                    kbest = k;
+            for (int q = 0; q < kMaxKPerLane; ++q) {
+                const int k = lane + 32 * q;
+                lo[q] = INFINITY;
+                if (k < T) {
+                    float l = cr[k], hi = cr[k];
+#pragma unroll
+                    for (int d = 1; d < 7; ++d) {
+                        l = fminf(l, cr[k + d]);
+                        hi = fmaxf(hi, cr[k + d]);
+                    }
+                    lo[q] = l;
+                    if (hi < ustar) {
+                        ustar = hi;
+                        kbest = k;
+                    }
                 }
             }
 #pragma unroll
@@ -205,15 +228,11 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
                 }
             }
             if (lane == 0) ka[r] = kbest < T ? kbest : 0;
-            for (int k0 = 0; k0 < T; k0 += 32) {
-                const int k = k0 + lane;
-                bool cand = false;
-                if (k < T) {
-                    float lo = cr[k];
 #pragma unroll
-                    for (int d = 1; d < 7; ++d) lo = fminf(lo, cr[k + d]);
-                    cand = !(lo > ustar);          // (non-finite rows keep every window)
-                }
+            for (int q = 0; q < kMaxKPerLane; ++q) {
+                const int k = lane + 32 * q;
+                if (32 * q >= T) break;
+                const bool cand = k < T && !(lo[q] > ustar);   // (non-finite rows keep every window)
                 const unsigned bal = __ballot_sync(0xffffffffu, cand);
                 int base = 0;
                 if (lane == 0 && bal) base = atomicAdd(count, __popc(bal));
@@ -272,6 +291,7 @@ cudaError_t setup_median(cg_plan_s* p)
 {
     p->median_ok = false;
     const int T = p->T;
+    if (T > 32 * kMaxKPerLane) return cudaSuccess;
     const int S = (T + 6) | 1;
     MedianArgs& m = p->med;
     m = MedianArgs{};
