@@ -493,7 +493,9 @@ cg_status cg_server_inject(cg_server_t server, int what, double value);
 /*
  * cg_stream_create -- an instrument stream on a server.
  *   plan          geometry and options (not owned; must outlive the stream and
- *                 is used only by the scheduler thread while the stream lives)
+ *                 is used only by the scheduler thread while the stream lives);
+ *                 each batch is one cg_process call, so with CG_INIT_MEDIAN the
+ *                 median filter's image is the batch
  *   ring_bytes    pinned host ring for the stream's frames (>= 2 batches)
  *   batch_frames  frames per batch (>= 1)
  *   max_delay_s   a partial batch is launched once its oldest frame has waited
