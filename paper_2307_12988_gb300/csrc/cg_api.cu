@@ -178,7 +178,7 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
         int bestF = 2;
         double best = 1e30;
         for (int F = 2; F <= 32; ++F) {
-            const int bytes = sb * N * F + 32 + 8 * L * F + 4 * T * F;
+            const int bytes = sb * N * F + 32 + 8 * L * F;
             if (bytes > 52 * 1024) break;
             const double cost =
                 (std::ceil(10.0 * F / 128.0) * 50.0 * Q + std::ceil(double(Q) * F / 128.0) * 200.0) / F;
@@ -196,7 +196,7 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
         a.sm_u = 0;
         a.sm_raw = off; off = align16(off + sb * N * bestF + 32);
         a.sm_Y = off; off = align16(off + 8 * L * bestF);
-        a.sm_amps = off; off = align16(off + 4 * T * bestF);
+        a.sm_amps = 0;
         a.sm_y = 0;
         a.sm_total = off;
         a.twL = p->d.tw_L;

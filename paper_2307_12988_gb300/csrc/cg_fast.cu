@@ -48,7 +48,6 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
     S* raw = reinterpret_cast<S*>(sm + a.sm_raw);
     const S* frames = static_cast<const S*>(a.frames);
     float2* Yb = reinterpret_cast<float2*>(sm + a.sm_Y);
-    float* amp_s = reinterpret_cast<float*>(sm + a.sm_amps);
     const int T = a.T, N = a.N, F = a.F;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         twL[i] = a.twL[i];
@@ -157,24 +156,20 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
                 z[q + 1] = make_float2(v.z, v.w);
             }
             Dft<P>::run(z);
+            // straight to global memory: the items of a frame hold runs of
+            // consecutive bins, i.e. runs of consecutive (or reversed) teeth
+            const int64_t orow = (f0 + f) * T;
 #pragma unroll
             for (int v = 0; v < P; ++v) {
                 const int k = tom[u + Q * v];
-                if (k >= 0) amp_s[f * T + k] = sqrtf(fmaf(z[v].x, z[v].x, z[v].y * z[v].y));
+                if (k >= 0) {
+                    const float av = sqrtf(fmaf(z[v].x, z[v].x, z[v].y * z[v].y));
+                    if (a.amps) a.amps[orow + k] = av;
+                    if (a.y) a.y[orow + k] = __fmul_rn(av, iref[k]);
+                }
             }
         }
-        __syncthreads();
-        // ---------------- outputs (coalesced) --------------------------------
-        {
-            int k = threadIdx.x % T;   // (frame, tooth) of flat index i, advanced incrementally
-            for (int i = threadIdx.x; i < nf * T; i += blockDim.x) {
-                const float av = amp_s[i];
-                if (a.amps) a.amps[f0 * T + i] = av;
-                if (a.y) a.y[f0 * T + i] = __fmul_rn(av, iref[k]);
-                k += blockDim.x;
-                while (k >= T) k -= T;
-            }
-        }
+        // (the next batch's stages start after the barrier at the loop top)
         off = offn;
     }
     cp_async_wait_all();
