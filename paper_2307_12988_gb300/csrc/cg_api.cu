@@ -184,6 +184,15 @@ cudaError_t setup_fast(cg_plan_s* p, const std::vector<int>& zidx)
                 (std::ceil(10.0 * F / 128.0) * 50.0 * Q + std::ceil(double(Q) * F / 128.0) * 200.0) / F;
             if (cost < best - 1e-9) { best = cost; bestF = F; }
         }
+        // frames per block measured best on GB300 for the instantiated
+        // transforms (occupancy and lane use trade against each other, which
+        // the idle-slot model above does not see): 10^6 paper-rate frames
+        // take 0.525 ms at F = 8 vs 0.547 ms at the model's 11; 8-bit
+        // 2200-sample frames 0.996 vs 1.08 ms; wide frames 0.624 vs 0.662 ms
+        struct Measured { int Q, sb, F; };
+        static const Measured kMeasured[] = {{10, 2, 12}, {11, 2, 8}, {22, 1, 8}, {25, 2, 5}};
+        for (const Measured& mf : kMeasured)
+            if (mf.Q == Q && mf.sb == sb && sb * N * mf.F + 32 + 8 * L * mf.F <= 52 * 1024) bestF = mf.F;
         a.N = N;
         a.T = T;
         a.F = bestF;
