@@ -213,8 +213,7 @@ MLP_BLOB = os.path.join(ROOT, "paper_2307_12988_gb300", "data", "mlp_wide_t221.c
 # DRAM bytes per frame measured by ncu on the paper-rate workload (kernel
 # names as in the per-kernel timing); the capture is summarised with its
 # command in profiles/paper_rate_traffic.md
-# (the fit kernel was rebuilt after its capture, so its traffic is not reported)
-NCU_TRAFFIC_PER_FRAME = {("paper_rate", "fft", "moment"): {"readout": 2520.2, "init": 396.3}}
+NCU_TRAFFIC_PER_FRAME = {("paper_rate", "fft", "moment"): {"readout": 2519.5, "init": 396.6, "fit": 415.7}}
 
 # FP32 operations of one LM point evaluation (model, residual, Jacobian and
 # the 14 running sums of J^T J, J^T r and chi^2): 11 + 10 FMA x 2 + 4 adds
