@@ -237,8 +237,10 @@ cg_status cg_readout_i8(cg_plan_t plan, const int8_t* frames_dev, int64_t n_fram
 /*
  * cg_fit -- only the initial guess and LM fit of cg_process, on normalised
  * spectra y_dev float [n][T].  p0_dev float [n][4] (abscissa units) or NULL
- * for the moment initial guess (CG_MODEL_FANO: not read; the fit makes its
- * own guess).  Outputs as in cg_process.
+ * for the plan's initial guess: the moments (CG_INIT_MOMENT), or the median
+ * filter over the call's n spectra as one time x tooth image
+ * (CG_INIT_MEDIAN); with CG_MODEL_FANO p0_dev is not read (the lowest tooth,
+ * or the median filter's centre).  Outputs as in cg_process.
  */
 cg_status cg_fit(cg_plan_t plan, const float* y_dev, int64_t n, const float* p0_dev,
                  float* params_dev, float* rss_dev, int16_t* iters_dev,
