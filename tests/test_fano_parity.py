@@ -8,7 +8,8 @@ paper-rate geometry; the oracle reads them out in FP64 and runs its
 box-constrained LM to convergence.  Bars: converged centres within 1e-4 of
 the linewidth; scale and offset within 1e-4 (their box edges reached on the
 same frames); the q = 0 case; a scale pushed past the box; ragged, empty
-and single-frame batches; lane counts; cg_fit on given spectra; refused
+and single-frame batches; lane counts; the FP64 solve and the tensor-core
+readout; cg_fit on given spectra; refused
 options.
 """
 import numpy as np
@@ -207,3 +208,12 @@ def test_fano_refused_options(dev):
                 fano_q=0.3, fano_gamma=GAMMA, fano_A=A_BAR, fano_B=B_BAR, init=cg.INIT_MLP)
     with pytest.raises(cg.CgError, match="CG_ERR_UNSUPPORTED"):
         _plan(w, lanes_per_frame=32)
+
+
+@pytest.mark.parametrize("opts", [dict(solve_f64=1), dict(readout=cg.READOUT_GEMM_SPLIT, sample_bits=12)])
+def test_fano_fp64_solve_and_tensor_core_readout(dev, opts):
+    # the FP64 3x3 solve (the GEMM readout's default) on one lane of the group
+    w = _w(-0.5)
+    with _plan(w, **opts) as p:
+        o = _process(p, w, dev, 0, 1000)
+    _compare(o, _oracle_fit(w, a=0, b=1000), f"fano {sorted(opts)}")
