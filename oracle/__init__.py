@@ -62,6 +62,8 @@ def _load():
         "or_dft_bins_f64": (i32, [P, i64, i32, i32, P, P, P]),
         "or_readout": (i32, [P, i64, i32, i32, P, P, P, P]),
         "or_reference": (i32, [P, i64, i32, i32, P, P]),
+        "or_readout_f64": (i32, [P, i64, i32, i32, P, P, P, P]),
+        "or_reference_f64": (i32, [P, i64, i32, i32, P, P]),
         "or_model": (None, [P, i32, P, P]),
         "or_jacobian": (None, [P, i32, P, P]),
         "or_moment_init": (i32, [P, P, i32, P]),
@@ -126,11 +128,25 @@ def dft_bins(frames, bins) -> tuple[np.ndarray, np.ndarray]:
     return re, im
 
 
-def readout(frames, bins, ref=None) -> tuple[np.ndarray, np.ndarray | None]:
-    """Tooth amplitudes |X_{b_k}| and, with ``ref``, normalised y_k = amps_k / ref_k."""
-    x = np.ascontiguousarray(frames, dtype=np.int16)
+def _frames(frames):
+    """Integer samples (int8, int16) as int16; floating point as FP64
+    (noise-free, unquantised input)."""
+    x = np.asarray(frames)
     if x.ndim == 1:
         x = x[None, :]
+    if np.issubdtype(x.dtype, np.integer):
+        if x.dtype.itemsize > 2:
+            raise TypeError("samples wider than 16 bits")
+        return np.ascontiguousarray(x, dtype=np.int16), True
+    return _f64(x), False
+
+
+def readout(frames, bins, ref=None) -> tuple[np.ndarray, np.ndarray | None]:
+    """Tooth amplitudes |X_{b_k}| and, with ``ref``, normalised y_k = amps_k / ref_k.
+
+    ``frames`` is int16 [n, N] (the digitised samples) or float [n, N]
+    (noise-free, unquantised input, read in FP64); ``ref`` is indexed by tooth."""
+    x, is16 = _frames(frames)
     n, N = x.shape
     b = np.ascontiguousarray(bins, dtype=np.int32)
     T = b.size
@@ -139,20 +155,25 @@ def readout(frames, bins, ref=None) -> tuple[np.ndarray, np.ndarray | None]:
     r = None
     if ref is not None:
         r = _f64(ref)
+        if r.size != T:
+            raise ValueError("ref must hold one value per tooth")
         y = np.empty((n, T))
-    rc = _load().or_readout(_p(x), n, N, T, _p(b), _p(r), _p(amps), _p(y))
+    fn = _load().or_readout if is16 else _load().or_readout_f64
+    rc = fn(_p(x), n, N, T, _p(b), _p(r), _p(amps), _p(y))
     if rc != 0:
         raise MemoryError
     return amps, y
 
 
 def reference(frames, bins) -> np.ndarray:
-    """Averaged reference spectrum: mean over cavity-free frames of |X_{b_k}|."""
-    x = np.ascontiguousarray(frames, dtype=np.int16)
+    """Averaged reference spectrum: mean over cavity-free frames of |X_{b_k}|
+    (int16 frames, or float frames read in FP64)."""
+    x, is16 = _frames(frames)
     n, N = x.shape
     b = np.ascontiguousarray(bins, dtype=np.int32)
     out = np.empty(b.size)
-    if _load().or_reference(_p(x), n, N, b.size, _p(b), _p(out)) != 0:
+    fn = _load().or_reference if is16 else _load().or_reference_f64
+    if fn(_p(x), n, N, b.size, _p(b), _p(out)) != 0:
         raise ValueError("no reference frames")
     return out
 

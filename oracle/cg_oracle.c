@@ -154,9 +154,23 @@ int or_dft_bins_f64(const double* x, int64_t n_frames, int N, int nb, const int*
     return 0;
 }
 
-/* amps_k = |X_{b_k}|;  y_k = amps_k / ref_k  (ref may be NULL: y not written) */
-int or_readout(const int16_t* x, int64_t n_frames, int N, int T, const int* bins,
-               const double* ref, double* amps, double* y)
+/* Readout of one frame's tooth bins: amps_k = |X_{b_k}| (the magnitude, not
+ * the power), y_k = amps_k / ref_k with ref indexed by tooth k, not by bin
+ * (ref may be NULL: y not written). */
+static void tooth_readout(const double* re, const double* im, int T, const double* ref,
+                          double* amps, double* y)
+{
+    for (int k = 0; k < T; ++k) {
+        double a = sqrt(re[k] * re[k] + im[k] * im[k]);
+        amps[k] = a;
+        if (ref && y) y[k] = a / ref[k];
+    }
+}
+
+/* frames are int16 (x16) or FP64 (x64, for noise-free unquantised input);
+ * exactly one of the two is given */
+static int readout_any(const int16_t* x16, const double* x64, int64_t n_frames, int N, int T,
+                       const int* bins, const double* ref, double* amps, double* y)
 {
     double* tc = (double*)malloc(sizeof(double) * (size_t)N);
     double* ts = (double*)malloc(sizeof(double) * (size_t)N);
@@ -168,12 +182,11 @@ int or_readout(const int16_t* x, int64_t n_frames, int N, int T, const int* bins
         double* im = (double*)malloc(sizeof(double) * (size_t)T);
 #pragma omp for schedule(dynamic, 16)
         for (int64_t i = 0; i < n_frames; ++i) {
-            dft_frame_i16(x + i * (int64_t)N, N, T, bins, tc, ts, re, im);
-            for (int k = 0; k < T; ++k) {
-                double a = sqrt(re[k] * re[k] + im[k] * im[k]);
-                amps[i * T + k] = a;
-                if (ref && y) y[i * T + k] = a / ref[k];
-            }
+            if (x16)
+                dft_frame_i16(x16 + i * (int64_t)N, N, T, bins, tc, ts, re, im);
+            else
+                dft_frame_f64(x64 + i * (int64_t)N, N, T, bins, tc, ts, re, im);
+            tooth_readout(re, im, T, ref, amps + i * T, y ? y + i * T : NULL);
         }
         free(re);
         free(im);
@@ -183,13 +196,28 @@ int or_readout(const int16_t* x, int64_t n_frames, int N, int T, const int* bins
     return 0;
 }
 
-/* reference spectrum: mean over cavity-free frames of |X_{b_k}| */
-int or_reference(const int16_t* x, int64_t n_frames, int N, int T, const int* bins, double* ref)
+int or_readout(const int16_t* x, int64_t n_frames, int N, int T, const int* bins,
+               const double* ref, double* amps, double* y)
+{
+    return readout_any(x, NULL, n_frames, N, T, bins, ref, amps, y);
+}
+
+int or_readout_f64(const double* x, int64_t n_frames, int N, int T, const int* bins,
+                   const double* ref, double* amps, double* y)
+{
+    return readout_any(NULL, x, n_frames, N, T, bins, ref, amps, y);
+}
+
+/* reference spectrum: the mean (sum / count) over cavity-free frames of the
+ * tooth magnitudes |X_{b_k}| -- a mean of magnitudes, not the magnitude of a
+ * mean spectrum */
+static int reference_any(const int16_t* x16, const double* x64, int64_t n_frames, int N, int T,
+                         const int* bins, double* ref)
 {
     if (n_frames < 1) return -1;
     double* amps = (double*)malloc(sizeof(double) * (size_t)n_frames * (size_t)T);
     if (!amps) return -1;
-    if (or_readout(x, n_frames, N, T, bins, NULL, amps, NULL) != 0) { free(amps); return -1; }
+    if (readout_any(x16, x64, n_frames, N, T, bins, NULL, amps, NULL) != 0) { free(amps); return -1; }
     for (int k = 0; k < T; ++k) {
         double s = 0.0;
         for (int64_t i = 0; i < n_frames; ++i) s += amps[i * T + k];
@@ -197,6 +225,16 @@ int or_reference(const int16_t* x, int64_t n_frames, int N, int T, const int* bi
     }
     free(amps);
     return 0;
+}
+
+int or_reference(const int16_t* x, int64_t n_frames, int N, int T, const int* bins, double* ref)
+{
+    return reference_any(x, NULL, n_frames, N, T, bins, ref);
+}
+
+int or_reference_f64(const double* x, int64_t n_frames, int N, int T, const int* bins, double* ref)
+{
+    return reference_any(NULL, x, n_frames, N, T, bins, ref);
 }
 
 /* ------------------------------------------------------------------ */

@@ -8,6 +8,11 @@ force, or an independent library routine, chosen so that a plausible slip
   the tooth bins): pure tone gives a N/2, X_0 = sum x, X_{N/2} = alternating
   sum, Parseval, numpy's rfft (real and imaginary parts, so the sign of the
   exponent is pinned too).
+* readout and reference, through ``oracle.readout`` / ``oracle.reference``
+  themselves: integer-valued tones at N/4 and N/6 give a N/2 and a N
+  (magnitude, not power) at teeth listed out of bin order, y divides by the
+  reference of the same tooth, the reference is the mean (not the sum) of
+  the frames' magnitudes (not the magnitude of their mean).
 * normalisation: noise-free unquantised frames divided by a cavity-free
   reference give the lineshape exactly.
 * Lorentzian model and Jacobian: values at x = c and |x-c| = g; central
@@ -89,6 +94,74 @@ def test_tooth_bins_on_grid_and_alias():
     assert bins[g.k.tolist().index(0)] == round(51e6 * 4096 / 2e9)
 
 
+def _c4(N, a, sine=False):
+    """a cos(pi n / 2) (or a sin): the integer sequence a, 0, -a, 0 -- a tone
+    at bin N/4 whose samples are exact int16 values."""
+    n = np.arange(N)
+    return a * (np.array([0, 1, 0, -1]) if sine else np.array([1, 0, -1, 0]))[n % 4]
+
+
+def _c6(N, a):
+    """2a cos(pi n / 3): the integer sequence 2a, a, -a, -2a, -a, a (bin N/6)."""
+    return a * np.array([2, 1, -1, -2, -1, 1])[np.arange(N) % 6]
+
+
+@pytest.mark.parametrize("N", [1200, 2400])
+def test_readout_exact_tones_by_tooth(N):
+    # teeth listed out of bin order; two tones of different amplitude
+    a1, a2 = 300, 200
+    x = (_c4(N, a1) + _c6(N, a2)).astype(np.int16)
+    bins = np.array([N // 6, N // 4, 0, N // 3], dtype=np.int32)
+    ref = np.array([2.0, 5.0, 1.0, 3.0])
+    amps, y = oracle.readout(x[None], bins, ref)
+    exp = np.array([a2 * N, a1 * N / 2, 0.0, 0.0])   # |2 a cos| -> a N, |a cos| -> a N / 2
+    np.testing.assert_allclose(amps[0], exp, rtol=1e-13, atol=1e-9 * a1 * N)
+    np.testing.assert_allclose(y[0], exp / ref, rtol=1e-13, atol=1e-9 * a1 * N)
+    # without ref no y; the FP64 entry reads the same integer samples alike
+    amps2, y2 = oracle.readout(x[None], bins)
+    assert y2 is None
+    np.testing.assert_array_equal(amps2, amps)
+    amps3, y3 = oracle.readout(x[None].astype(np.float64), bins, ref)
+    np.testing.assert_array_equal(amps3, amps)
+    np.testing.assert_array_equal(y3, y)
+    with pytest.raises(ValueError):
+        oracle.readout(x[None], bins, ref[:3])
+
+
+def test_readout_rows_independent():
+    # frame i of a batch reads the same as frame i alone
+    N = 1200
+    rng = np.random.default_rng(5)
+    x = rng.integers(-2048, 2048, (5, N)).astype(np.int16)
+    bins = np.array([7, 300, 200, 1, 600], dtype=np.int32)
+    ref = rng.uniform(0.5, 2.0, bins.size)
+    amps, y = oracle.readout(x, bins, ref)
+    for i in range(5):
+        a1, y1 = oracle.readout(x[i], bins, ref)
+        np.testing.assert_array_equal(a1[0], amps[i])
+        np.testing.assert_array_equal(y1[0], y[i])
+    re, im = oracle.dft_bins(x, bins)
+    np.testing.assert_allclose(amps, np.hypot(re, im), rtol=1e-15)
+
+
+def test_reference_is_mean_of_magnitudes():
+    N = 1200
+    amps_in = [100, -300, 500]                  # a negative amplitude has magnitude |a|
+    rows = [_c4(N, amps_in[0]), _c4(N, amps_in[1], sine=True), _c4(N, amps_in[2])]
+    x = np.stack(rows).astype(np.int16)
+    bins = np.array([N // 4, N // 6], dtype=np.int32)
+    ref = oracle.reference(x, bins)
+    # mean of |a_i| N / 2 (a sum would be 3x; the magnitude of the mean spectrum
+    # |(100 + 500)/3 + i 300/3| N / 2 differs as well)
+    assert abs(ref[0] - np.mean(np.abs(amps_in)) * N / 2) <= 1e-12 * 500 * N
+    assert abs(ref[1]) <= 1e-9 * 500 * N
+    # one frame: the reference is that frame's readout
+    one = oracle.reference(x[:1], bins)
+    np.testing.assert_array_equal(one, oracle.readout(x[:1], bins)[0][0])
+    with pytest.raises(ValueError):
+        oracle.reference(x[:0], bins)
+
+
 def test_normalisation_noise_free_gives_lineshape():
     g = synth.PAPER_RATE
     N, fs = g.frame_len, g.sample_rate
@@ -106,6 +179,16 @@ def test_normalisation_noise_free_gives_lineshape():
     re0, im0 = oracle.dft_bins(refr[None], bins)
     y = np.hypot(re1, im1)[0] / np.hypot(re0, im0)[0]
     np.testing.assert_allclose(y, L, rtol=0, atol=1e-12)
+    # the same through the oracle's own readout and reference: three
+    # cavity-free frames whose phases differ (equal magnitudes, so the mean
+    # of magnitudes is each frame's), then the normalised cavity frame
+    refs = np.stack([env @ np.cos(2 * np.pi * np.outer(g.tooth_freqs, n) / fs + ph[:, None] + s)
+                     for s in (0.0, 0.7, 2.1)])
+    ref = oracle.reference(refs, bins)
+    np.testing.assert_allclose(ref, np.hypot(re0, im0)[0], rtol=1e-12)
+    amps, y2 = oracle.readout(cav[None], bins, ref)
+    np.testing.assert_allclose(y2[0], L, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(amps[0], np.hypot(re1, im1)[0], rtol=1e-13)
 
 
 def test_model_closed_forms():

@@ -128,8 +128,7 @@ def test_lm_parity_from_oracle_init(dev, lanes):
         status = out["status"].cpu().numpy()
         iters = out["iters"].cpu().numpy()
     conv = w["converged"]["params"]
-    ok = status == cg.FIT_CONVERGED
-    assert ok.mean() >= 0.99
+    ok = W.judge_fit(params, status, w["oracle"], w["converged"], CENTER_TOL, f"lm lanes={lanes}")
     assert np.max(np.abs(params[ok, 0] - conv[ok, 0])) <= CENTER_TOL
     assert np.max(np.abs(params[ok, 1] - conv[ok, 1])) <= CENTER_TOL
     assert np.max(np.abs(params[ok, 2:] - conv[ok, 2:])) <= 1e-4
@@ -148,8 +147,7 @@ def test_process_parity(dev, name, path):
         o = {k: v.cpu().numpy() for k, v in out.items() if v is not None}
     assert _amp_err(o["amps"], w) <= AMP_TOL
     assert np.max(np.abs(o["y"] - w["oracle"]["y"])) <= AMP_TOL
-    ok = o["status"] == cg.FIT_CONVERGED
-    assert ok.mean() >= 0.99, np.bincount(o["status"])
+    ok = W.judge_fit(o["params"], o["status"], w["oracle"], w["converged"], CENTER_TOL, f"{name} path {path}")
     conv = w["converged"]["params"]
     assert np.max(np.abs(o["params"][ok, 0] - conv[ok, 0])) <= CENTER_TOL
     # secondary parameters: the chi^2 stopping rule (tol 1e-6) leaves the flatter

@@ -47,3 +47,29 @@ def workload(name: str) -> dict:
 def plan_args(w: dict) -> tuple:
     g = w["geom"]
     return (g.sample_rate, g.frame_len, g.tooth_freqs, g.tooth_x, w["ref"])
+
+
+def judge_fit(params, status, capped, conv, center_tol, label="", c_col=0):
+    """Judge every frame of a GPU fit against the oracle.
+
+    * the status of each frame (low two bits: converged, max_iter, singular,
+      non-finite) equals the oracle's iteration-capped run of the same frame;
+    * a converged frame's centre lies within ``center_tol`` of the oracle's
+      fully converged optimum (``conv``, which must have converged too);
+    * any other frame's centre lies within ``center_tol`` of the oracle's
+      capped result (the two runs stopped at the same kind of point).
+    ``c_col`` is the centre's column in the oracle's parameter rows.
+    Returns the mask of converged frames."""
+    st = np.asarray(status).astype(np.int64) & 3
+    ost = np.asarray(capped["status"]).astype(np.int64) & 3
+    bad = np.flatnonzero(st != ost)
+    assert bad.size == 0, (
+        f"{label}: status differs from the oracle's capped run on {bad.size} frames "
+        f"(first {bad[:5].tolist()}: gpu {st[bad[:5]].tolist()}, oracle {ost[bad[:5]].tolist()}); "
+        f"histograms gpu {np.bincount(st, minlength=4).tolist()}, oracle {np.bincount(ost, minlength=4).tolist()}")
+    ok = st == 0
+    assert np.all(np.asarray(conv["status"])[ok] & 3 == 0), f"{label}: oracle optimum not converged"
+    want = np.where(ok, np.asarray(conv["params"])[:, c_col], np.asarray(capped["params"])[:, c_col])
+    dc = np.abs(np.asarray(params)[:, 0] - want)
+    assert np.all(dc <= center_tol), (label, float(dc.max()), int(np.argmax(dc)))
+    return ok
