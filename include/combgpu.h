@@ -247,9 +247,9 @@ cg_status cg_fit(cg_plan_t plan, const float* y_dev, int64_t n, const float* p0_
                  int16_t* status_dev, void* cuda_stream);
 
 /*
- * cg_reference_accumulate -- averaged reference spectrum (paper: "a
- * pre-calculated average reference spectrum, typically recorded at the
- * beginning of the experiment"): ref_host[k] = mean over the n cavity-free
+ * cg_reference_accumulate -- the averaged cavity-free reference spectrum that
+ * each spectrum is divided by ("Data Capture and Processing"; recorded once,
+ * before the measurement): ref_host[k] = mean over the n cavity-free
  * frames of |X_{b_k}|, accumulated in FP64 on the device.  Blocks until the
  * result is in ref_host (double [T]).  Does not change the plan's reference.
  */
@@ -264,9 +264,10 @@ cg_status cg_reference_accumulate(cg_plan_t plan, const int16_t* frames_dev, int
  * does not own, or a host application that lends the library only a stream
  * and buffers.  The paper has no counterpart; this is a convenience of the
  * library's interface.
- *   frames_dev  int16 [n][N] cavity-free frames on the plan's device, n >= 1
- *   ref_dev     double [n_teeth] on the plan's device, 8-byte aligned:
- *               receives mean |X_{b_k}| (the caller owns it)
+ *   frames_dev  int16 [n][N] cavity-free frames in device memory of the
+ *               plan's device, n >= 1
+ *   ref_dev     double [n_teeth] in device memory of the plan's device,
+ *               8-byte aligned: receives mean |X_{b_k}| (the caller owns it)
  * Allocates nothing and calls no allocating routine.  Its scratch is one array
  * of 32768 doubles (256 KiB) compiled into the library, present on every GPU
  * that loads it until the process exits; each call uses at most
@@ -274,10 +275,14 @@ cg_status cg_reference_accumulate(cg_plan_t plan, const int16_t* frames_dev, int
  * 32768 would be rejected with CG_ERR_ARG.  Every call shares that array:
  * two calls whose work overlaps on the GPU (other streams, other threads)
  * race and give wrong results, so serialise them.  Each call writes every
- * scratch value it reads, so nothing needs clearing between calls.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Asynchronous on
- * cuda_stream; errors: CG_ERR_ARG, CG_ERR_UNSUPPORTED, CG_ERR_CUDA.
+ * scratch value it reads, so nothing needs clearing between calls.  The
+ * set-up is done by cg_plan, which may allocate: with the plan's device
+ * current it looks up the array's device address (cudaGetSymbolAddress),
+ * which also loads the array onto the device, loads the accumulation
+ * kernels, and keeps the address in the plan; this entry point only reads
+ * it.  Pointers that are not device memory of the plan's device are
+ * refused (CG_ERR_ARG) before any launch.  Asynchronous on cuda_stream;
+ * errors: CG_ERR_ARG, CG_ERR_UNSUPPORTED, CG_ERR_CUDA.
  */
 cg_status cg_reference_accumulate_noalloc(cg_plan_t plan, const int16_t* frames_dev,
                                           int64_t n, double* ref_dev, void* cuda_stream);

@@ -20,6 +20,7 @@ _lock = threading.Lock()
 _lib = None
 
 CG_OK = 0
+CG_ERR_ARG = 1
 STATUS_NAMES = {0: "CG_OK", 1: "CG_ERR_ARG", 2: "CG_ERR_CUDA", 3: "CG_ERR_NOMEM",
                 4: "CG_ERR_TOOTH_RANGE", 5: "CG_ERR_OVERFLOW", 6: "CG_ERR_TIMEOUT",
                 7: "CG_ERR_DEVICE_CHECK", 8: "CG_ERR_UNSUPPORTED", 9: "CG_ERR_STATE"}
@@ -316,7 +317,29 @@ def cg_reference_accumulate(plan: int, frames, n: int, stream=None) -> np.ndarra
 
 def cg_reference_accumulate_noalloc(plan: int, frames, n: int, ref_dev, stream=None) -> None:
     """Reference average into the caller's device buffer ``ref_dev`` (float64
-    [n_teeth]) without any allocation by the library (see the C header)."""
+    [n_teeth]) without any allocation by the library (see the C header).
+
+    ``frames`` (int16, at least n * frame_len elements) and ``ref_dev``
+    (float64, contiguous, at least n_teeth elements) must be CUDA tensors on
+    one device; anything else raises CgError before the call."""
+    info = cg_plan_describe(plan)
+    need_frames = int(n) * info["frame_len"]
+
+    def _bad(what):
+        raise CgError(CG_ERR_ARG, "cg_reference_accumulate_noalloc", what)
+
+    for name, t, dtype, count in (("frames", frames, "torch.int16", need_frames),
+                                  ("ref_dev", ref_dev, "torch.float64", info["n_teeth"])):
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            _bad(f"{name} must be a CUDA tensor")
+        if str(t.dtype) != dtype:
+            _bad(f"{name} must be {dtype}, not {t.dtype}")
+        if not t.is_contiguous():
+            _bad(f"{name} must be contiguous")
+        if t.numel() < count:
+            _bad(f"{name} holds {t.numel()} elements, needs {count}")
+    if frames.device != ref_dev.device:
+        _bad("frames and ref_dev are on different devices")
     _check(load().cg_reference_accumulate_noalloc(plan, _ptr(frames), int(n), _ptr(ref_dev),
                                                   _stream(stream)),
            "cg_reference_accumulate_noalloc")

@@ -671,6 +671,12 @@ cg_status cg_plan(cg_plan_t* out, double fs, int N, int T, const double* tooth_f
         free_plan(p);
         return fail(CG_ERR_UNSUPPORTED, "the learned initial guess needs the fit kernels and n_teeth <= 256");
     }
+    // the allocation-free reference entry point's set-up (address lookup and
+    // module loads), so that its calls neither allocate nor load anything
+    if ((e = cg::bind_noalloc_scratch(p)) != cudaSuccess || (e = cg::preload_reference_kernels(p)) != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "allocation-free scratch set-up");
+    }
     *out = p;
     return CG_OK;
 }

@@ -276,6 +276,8 @@ struct cg_plan_s {
     CUtensorMap mlp_map{};
     int mlp_smem = 0;
     cg::MlpArgs ma{};
+    // device address of the allocation-free reference scratch (set by cg_plan)
+    double* noalloc_scratch = nullptr;
     // per-kernel timing
     bool timing = false;
     struct TimedLaunch {
@@ -303,6 +305,11 @@ cudaError_t launch_reference(const cg_plan_s* p, const int16_t* frames, int64_t 
 // T doubles) and output (T doubles), both device memory
 cudaError_t launch_reference_into(const cg_plan_s* p, const int16_t* frames, int64_t n,
                                   double* part, int max_rows, double* out, cudaStream_t s);
+// loads the reference-accumulation kernels of the plan's lane count (no launch)
+cudaError_t preload_reference_kernels(const cg_plan_s* p);
+// looks up the allocation-free scratch array on the plan's device (which must
+// be current) and keeps its address in the plan
+cudaError_t bind_noalloc_scratch(cg_plan_s* p);
 
 FitArgs make_fit_args(const cg_plan_s* p);
 

@@ -416,6 +416,16 @@ cudaError_t launch_reference(const cg_plan_s* p, const int16_t* frames, int64_t 
     return cudaGetLastError();
 }
 
+cudaError_t preload_reference_kernels(const cg_plan_s* p)
+{
+    // querying a kernel's attributes loads its module (lazy loading), so the
+    // first launch later needs no module load
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, readout_ptr(2, p->G));
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(&ref_reduce_kernel));
+    return e;
+}
+
 cudaError_t launch_reference_into(const cg_plan_s* p, const int16_t* frames, int64_t n,
                                   double* part, int max_rows, double* out, cudaStream_t s)
 {

@@ -11,10 +11,11 @@
 //
 // The array lives in device memory of every GPU that loads the library, for
 // as long as the process lives.  Host code may not use its name as a device
-// address, so its address is looked up once per device with
-// cudaGetSymbolAddress and cached; the first call on each device does that.
+// address: cg_plan looks the address up (cudaGetSymbolAddress, the plan's
+// device current), which also loads the array onto that device, and keeps it
+// in the plan.  A plan made after a device reset therefore holds the address
+// of that reset's reload; the entry point itself looks nothing up.
 #include <cstdint>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -25,26 +26,8 @@ namespace {
 // 32768 doubles = 256 KiB of partial sums: rows of n_teeth values, one row
 // per thread block of the accumulation kernel.
 constexpr int kNoAllocScratchDoubles = 32768;
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) double g_ref_scratch[kNoAllocScratchDoubles];
-
-std::mutex g_scratch_mu;
-double* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_ref_scratch on `dev` (looked up with `dev` current).
-cudaError_t scratch_on(int dev, double** out)
-{
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (g_scratch_addr[dev] == nullptr) {
-        void* ptr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_ref_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<double*>(ptr);
-    }
-    *out = g_scratch_addr[dev];
-    return cudaSuccess;
-}
 
 cg_status noalloc_fail(cg_status st, const char* msg)
 {
@@ -52,7 +35,32 @@ cg_status noalloc_fail(cg_status st, const char* msg)
     return st;
 }
 
+// true when ptr is device (or managed) memory that the plan's device can use
+bool on_plan_device(const void* ptr, int device)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();   // clear the (non-sticky) error an unknown pointer leaves
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == device;
+}
+
 }  // namespace
+
+namespace cg {
+
+cudaError_t bind_noalloc_scratch(cg_plan_s* p)
+{
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_ref_scratch);
+    if (e != cudaSuccess) return e;
+    p->noalloc_scratch = static_cast<double*>(ptr);
+    return cudaSuccess;
+}
+
+}  // namespace cg
 
 extern "C" {
 
@@ -71,16 +79,17 @@ cg_status cg_reference_accumulate_noalloc(cg_plan_t plan, const int16_t* frames_
     const int rows = kNoAllocScratchDoubles / T;
     if (rows < 1)
         return noalloc_fail(CG_ERR_ARG, "n_teeth exceeds the 32768-double static scratch");
-    if (plan->device < 0 || plan->device >= kMaxDevices)
-        return noalloc_fail(CG_ERR_UNSUPPORTED, "device ordinal beyond 63");
+    if (!plan->noalloc_scratch) return noalloc_fail(CG_ERR_CUDA, "the plan holds no scratch address");
+    if (!on_plan_device(frames_dev, plan->device))
+        return noalloc_fail(CG_ERR_ARG, "frames_dev is not device memory of the plan's device");
+    if (!on_plan_device(ref_dev, plan->device))
+        return noalloc_fail(CG_ERR_ARG, "ref_dev is not device memory of the plan's device");
 
     int prev = -1;
     cudaError_t e = cudaGetDevice(&prev);
     if (e == cudaSuccess && prev != plan->device) e = cudaSetDevice(plan->device);
-    double* scratch = nullptr;
-    if (e == cudaSuccess) e = scratch_on(plan->device, &scratch);
     if (e == cudaSuccess)
-        e = cg::launch_reference_into(plan, frames_dev, n, scratch, rows, ref_dev,
+        e = cg::launch_reference_into(plan, frames_dev, n, plan->noalloc_scratch, rows, ref_dev,
                                       static_cast<cudaStream_t>(cuda_stream));
     if (prev >= 0 && prev != plan->device) cudaSetDevice(prev);
     if (e != cudaSuccess) {
