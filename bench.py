@@ -210,10 +210,10 @@ def build_workload(args, n_frames, n_ref, device, seed_offset=0):
 
 MLP_BLOB = os.path.join(ROOT, "paper_2307_12988_gb300", "data", "mlp_wide_t221.cgmlp")
 
-# DRAM bytes per frame measured by ncu on the paper-rate workload (kernel
-# names as in the per-kernel timing); the capture is summarised with its
-# command in profiles/paper_rate_traffic.md
-NCU_TRAFFIC_PER_FRAME = {("paper_rate", "fft", "moment"): {"readout": 2519.5, "init": 396.6, "fit": 415.7}}
+# DRAM bytes per frame (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# ncu capture of each kernel on the paper-rate workload, by the stage names
+# of the per-kernel timing; a kernel changed since its capture has none
+NCU_TRAFFIC_PER_FRAME = {("paper_rate", "fft", "moment"): {"readout": 2519.5, "init": 396.6}}
 
 # FP32 operations of one LM point evaluation (model, residual, Jacobian and
 # the 14 running sums of J^T J, J^T r and chi^2): 11 + 10 FMA x 2 + 4 adds
@@ -223,10 +223,19 @@ LM_FLOP_PER_POINT = 35
 LM_FLOP_PER_POINT_FANO = 33
 
 
-def kernel_rooflines(stage_ms, stage_launches, n, g, T, args, mean_iters, hbm, bf16):
+def alu_peak_measured(cg) -> dict:
+    """FP32 fused multiply-add throughput measured on this device now
+    (cg_fp32_peak: scalar and packed FP32x2 chains, CUDA events); the larger
+    of the two is the ALU roofline's denominator."""
+    scalar = cg.cg_fp32_peak(False, 20)
+    packed = cg.cg_fp32_peak(True, 20)
+    return {"tflops": max(scalar, packed), "scalar_tflops": scalar, "packed_tflops": packed,
+            "kind": "measured (cg_fp32_peak, FMA chains, CUDA events)"}
+
+
+def kernel_rooflines(stage_ms, stage_launches, n, g, T, args, mean_iters, hbm, bf16, alu_peak):
     """Per-kernel figures from the timing pass: mean launch time and the
     roofline each is bound by (algorithmic work / launch time)."""
-    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12       # FP32 FMA lanes x 2 flop x max SM clock, TFLOP/s
     out = {}
     for st, ms in stage_ms.items():
         cnt = stage_launches[st]
@@ -368,10 +377,11 @@ def run_ours(args):
     mean_iters = float(iters.float().mean().item())
 
     hbm, bf16, peak_kind = _peaks()
+    alu = alu_peak_measured(cg)
     sb = args.sample_bytes
     bytes_per_frame = sb * g.frame_len + 4 * T + 16 + 4 + 2 + 2
     kern = kernel_rooflines({k: v[0] for k, v in stages.items()}, {k: v[1] for k, v in stages.items()},
-                            n, g, T, args, mean_iters, hbm, bf16)
+                            n, g, T, args, mean_iters, hbm, bf16, alu["tflops"])
     dominant = max(kern, key=lambda k: kern[k]["launches"] * kern[k]["ms_per_launch"])
     dom = kern[dominant]
     total_frames = n * ws
@@ -396,7 +406,9 @@ def run_ours(args):
         "input_gbs": total_frames * sb * g.frame_len / (ms_step / 1e3) / 1e9,
         "roofline": {"kernel": dominant, "bound": dom.get("bound"), "achieved": dom.get("achieved"),
                      "peak": dom.get("peak"), "unit": dom.get("unit"), "frac": dom.get("frac"),
-                     "traffic": dom.get("traffic"), "peak_kind": peak_kind},
+                     "traffic": dom.get("traffic"),
+                     "peak_kind": alu["kind"] if dom.get("bound") == "alu" else peak_kind},
+        "alu_peak": alu,
         "step_hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "algorithmic_bytes_per_frame": bytes_per_frame},
         "kernels": kern,
@@ -665,7 +677,8 @@ def run_psd(args):
     L = M // 2
     flops = K * 5.0 * L * math.log2(L)                    # the complex transform of every segment
     achieved = flops / (ms / 1e3) / 1e12
-    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    alu = alu_peak_measured(cg)
+    alu_peak = alu["tflops"]
     # end to end: the series from pinned host memory, the PSD and fit back
     xh = x.cpu().pin_memory()
     torch.cuda.synchronize()
@@ -696,7 +709,8 @@ def run_psd(args):
                       "steps": int(res[9]), "status": int(res[10])},
         "roofline": {"kernel": "psd_welch_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak,
                      "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
-                     "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)"},
+                     "peak_kind": alu["kind"]},
+        "alu_peak": alu,
         "input_gbs": 4.0 * n / (ms / 1e3) / 1e9,
         "input_hbm_frac": 4.0 * n / (ms / 1e3) / 1e9 / hbm,
         "cpu_baseline": {"value": sample.size / cpu_s, "unit": "samples/s", "cores": 1, "kind": "oracle",
@@ -736,7 +750,7 @@ def main():
     ap.add_argument("--e2e-chunk", type=int, default=65536)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-impl-frames", type=int, default=20000)
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="streaming leg duration (the serving workload runs 60 s per stream)")
     ap.add_argument("--serve-only", action="store_true", help="run only the streaming leg")
     ap.add_argument("--serve-batch", type=int, default=4096)

@@ -318,6 +318,19 @@ cg_status cg_timing_enable(cg_plan_t plan, int enable);
 cg_status cg_timing_collect(cg_plan_t plan, double* ms_host, int64_t* launches_host);
 
 /*
+ * cg_fp32_peak -- measured FP32 fused multiply-add throughput of the current
+ * device, the denominator of the LM kernels' ALU roofline (a diagnostic; the
+ * paper has no counterpart).  Launches, on cuda_stream, one warm-up and then
+ * reps timed launches of a kernel whose threads each run 16 independent
+ * chains a <- a m + c (packed = 1: 8 chains of FP32x2 pairs, one instruction
+ * per two fused multiply-adds), 4 blocks of 256 threads per SM, and writes
+ * 2 x fused multiply-adds / elapsed time (CUDA events) to *tflops_host in
+ * TFLOP/s.  Blocks until done.  Allocates no device memory.  Errors:
+ * CG_ERR_ARG (packed not 0 or 1, reps < 1, NULL output), CG_ERR_CUDA.
+ */
+cg_status cg_fp32_peak(int packed, int reps, double* tflops_host, void* cuda_stream);
+
+/*
  * ---- Learned initial guess -------------------------------------------------
  * A multilayer perceptron n_in -> H -> H -> n_out with tanh-form GELU hidden
  * activations (z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))) and a linear

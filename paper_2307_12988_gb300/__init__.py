@@ -20,6 +20,7 @@ from ._binding import (cg_mlp_adam, cg_mlp_backward, cg_mlp_create, cg_mlp_destr
                        cg_mlp_set_norm, cg_mlp_set_params, cg_mlp_train_epoch, cg_timing_collect,
                        cg_timing_enable)
 from ._binding import cg_psd_create, cg_psd_destroy, cg_psd_welch, cg_resonance_fit
+from ._binding import cg_fp32_peak
 from ._binding import (RESULT_DTYPE, INJECT_FAIL_LAUNCH, INJECT_HOLD, INJECT_THROTTLE_S, cg_clock,
                        cg_server_create, cg_server_destroy, cg_server_inject, cg_stream_create,
                        cg_stream_destroy, cg_stream_flush, cg_stream_poll, cg_stream_push,

@@ -110,6 +110,7 @@ _SIGS = {
     "cg_reference_accumulate_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     "cg_check_device": (ctypes.c_int, [_P]),
     "cg_timing_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cg_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
     "cg_timing_collect": (ctypes.c_int, [_P, _P, _P]),
     "cg_mlp_param_count": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "cg_mlp_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -348,6 +349,14 @@ def cg_reference_accumulate_noalloc(plan: int, frames, n: int, ref_dev, stream=N
 def cg_check_device(plan: int) -> None:
     """Synchronise and raise CgError if a kernel recorded a device-side error."""
     _check(load().cg_check_device(plan), "cg_check_device")
+
+
+def cg_fp32_peak(packed: bool, reps: int = 20, stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device in TFLOP/s."""
+    out = ctypes.c_double(0.0)
+    _check(load().cg_fp32_peak(1 if packed else 0, int(reps), ctypes.byref(out), _stream(stream)),
+           "cg_fp32_peak")
+    return float(out.value)
 
 
 def cg_timing_enable(plan: int, enable: bool) -> None:

@@ -303,6 +303,11 @@ cudaError_t setup_fit_kernels(cg_plan_s* p)
         if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
     p->G2 = G;
     p->PPL = ppl;
+    // the Lorentzian with the FP32 solve and lanes per frame left to the
+    // library: the shared-memory kernel where it is instantiated
+    if (p->opts.lanes_per_frame == 0 && model == CG_MODEL_LORENTZ && !p->solve_f64 &&
+        (e = cg::setup_fit3(p)) != cudaSuccess)
+        return e;
     // 0: the whole call is one chunk (one launch per kernel; measured fastest
     // for large calls, since each kernel then has frames enough for every SM)
     p->chunk = p->opts.chunk_frames ? p->opts.chunk_frames : (int64_t(1) << 40);
@@ -711,7 +716,7 @@ cg_status cg_plan_describe(cg_plan_t p, cg_plan_info* info, int* bins_host)
                : (p->opts.path == CG_PATH_PIPELINE && !p->fit_ok) ? CG_PATH_FUSED : p->opts.path;
     if (p->opts.readout != CG_READOUT_FFT || p->opts.init != CG_INIT_MOMENT || p->opts.model == CG_MODEL_FANO)
         info->path = CG_PATH_PIPELINE;
-    if (info->path == CG_PATH_PIPELINE) info->lanes_per_frame = p->G2;
+    if (info->path == CG_PATH_PIPELINE) info->lanes_per_frame = p->fit3_ok ? p->fit3_G : p->G2;
     if (bins_host) std::memcpy(bins_host, p->bins.data(), sizeof(int) * p->T);
     return CG_OK;
 }

@@ -113,6 +113,9 @@ struct Fit2Args {
     // their averages (the starting values)
     float fano_q, fano_g, fano_inv_g, fano_shift;
     float fano_A0, fano_B0, fano_Alo, fano_Ahi, fano_Blo, fano_Bhi;
+    // rows of the y / amps buffer (the shared-memory kernel's copies stay inside it)
+    int64_t n_rows;
+    int* err;                // device error word (a row copy that never landed)
 };
 
 // Arguments of the learned initial-guess inference kernel (cg_mlp_tc.cu).
@@ -261,6 +264,8 @@ struct cg_plan_s {
     int solve_f64 = 0;
     cg::GemmArgs ga{};
     int Q = 0;               // L = 10 Q
+    bool fit3_ok = false;    // shared-memory LM kernel (cg_fit3.cu) configured
+    int fit3_G = 0, fit3_warps = 0, fit3_smem = 0, grid_fit3 = 0;
     int G2 = 4;              // LM lanes per frame of the register-resident fit
     int PPL = 0;             // LM points per lane
     bool ppl_exact = false;  // PPL == ceil(T / G2)
@@ -343,6 +348,10 @@ cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, i
                         const float* p0, const int16_t* flags_in, float* params, float* rss,
                         int16_t* iters, int16_t* status, cudaStream_t s,
                         const FitLaunch& fl = FitLaunch());
+// the shared-memory LM kernel: set-up at plan creation, launch with the
+// arguments launch_fit2 prepared
+cudaError_t setup_fit3(cg_plan_s* p);
+cudaError_t launch_fit3(const cg_plan_s* p, Fit2Args a, cudaStream_t s);
 
 // learned initial guess (cg_mlp_tc.cu)
 cudaError_t setup_mlp(cg_plan_s* p, const unsigned char* blob, size_t bytes, const char** why);

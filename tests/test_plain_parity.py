@@ -207,3 +207,36 @@ def test_results_independent_of_requesting_y(dev, name):
         torch.cuda.synchronize()
         for k in ("amps", "params", "rss", "iters", "status"):
             np.testing.assert_array_equal(with_y[k].cpu().numpy(), no_y[k].cpu().numpy(), err_msg=k)
+
+
+def _all_values_frames(lo, hi, N, dtype, seed):
+    """Frames of N samples holding every integer of [lo, hi] once (in random
+    order), padded with random values to whole frames."""
+    rng = np.random.default_rng(seed)
+    vals = rng.permutation(np.arange(lo, hi + 1, dtype=np.int64))
+    nf = -(-vals.size // N)
+    pad = rng.integers(lo, hi + 1, nf * N - vals.size)
+    return np.concatenate([vals, pad]).astype(dtype).reshape(nf, N)
+
+
+@pytest.mark.parametrize("name", ["tiny", "paper_rate", "wide", "serve4096", "paper8"])
+def test_default_readout_full_sample_range(dev, name):
+    # every int16 value (every int8 value for the 8-bit frame) through the
+    # default readout of each geometry (coset-pruned transform; the
+    # power-of-two transform for 4096 samples): the cast is exact, so the
+    # amplitudes meet the oracle's within the FP32 transform's rounding,
+    # bounded here by 1e-5 of the frame's root-sum-square amplitude
+    w = W.workload(name)
+    g = w["geom"]
+    if name == "paper8":
+        fr = _all_values_frames(-128, 127, g.frame_len, np.int8, 19)
+        fr = np.concatenate([fr] * 8)
+    else:
+        fr = _all_values_frames(-32768, 32767, g.frame_len, np.int16, 17)
+    amps_o, _ = oracle.readout(fr, w["bins"])
+    with _plan(w) as p:
+        amps, _ = p.readout(torch.from_numpy(fr).to(dev), want_y=False)
+        cg.cg_check_device(p.handle)
+    scale = np.sqrt(g.frame_len * (fr.astype(np.float64) ** 2).sum(axis=1, keepdims=True))
+    err = np.max(np.abs(amps.cpu().numpy() - amps_o) / scale)
+    assert err <= 1e-5, (name, err)
