@@ -23,7 +23,14 @@
 //    the summation order depends on the tooth index only, not on where the
 //    frame lies in memory: a frame's result is the same in any batch.
 //  * per pair, one 16-byte table entry gives both abscissae and both
-//    1 / reference values (1 when the normalised spectra are given).
+//    1 / reference values (1 when the normalised spectra are given);
+//  * the point is evaluated in e = (u - c) / g: L = 1 / (1 + e^2) takes two
+//    packed operations and a reciprocal; the centre column L q d (q the
+//    reciprocal of (u - c)^2 + g^2) equals L^2 e / g and the width column
+//    L q d^2 equals L (1 - L), so per point the sums are of L^2, L^3, L^4,
+//    L, L jc', L^2 jc', jc'^2, jc', L r, jc' r, L^2 r, r, r^2 with
+//    jc' = L^2 e (13 instead of 14, and no separate L q product); the 14
+//    sums of the textbook normal equations follow from them per frame.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -45,6 +52,27 @@ __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 mul2_rounded(float2 a, float2 b)
 {
     return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+}
+
+// The 14 sums of fit2_kernel (L L, L jc, L jg, L, jc jc, jc jg, jc, jg jg,
+// jg, L r, jc r, jg r, r, r r with jc = L q d and jg = jc d) from the 13
+// sums over L, L^2 and jc' = L^2 e = g jc, using jg = L - L^2.
+__device__ __forceinline__ void sums_from_powers(const float (&w)[13], float ig, LmSums& S)
+{
+    S.v[0] = w[0];                                  // L L
+    S.v[1] = w[4] * ig;                             // L jc
+    S.v[2] = w[0] - w[1];                           // L jg = L^2 - L^3
+    S.v[3] = w[3];                                  // L
+    S.v[4] = w[6] * (ig * ig);                      // jc jc
+    S.v[5] = (w[4] - w[5]) * ig;                    // jc jg
+    S.v[6] = w[7] * ig;                             // jc
+    S.v[7] = fmaf(-2.0f, w[1], w[0]) + w[2];        // jg jg = L^2 - 2 L^3 + L^4
+    S.v[8] = w[3] - w[0];                           // jg = L - L^2
+    S.v[9] = w[8];                                  // L r
+    S.v[10] = w[9] * ig;                            // jc r
+    S.v[11] = w[8] - w[10];                         // jg r = L r - L^2 r
+    S.v[12] = w[11];                                // r
+    S.v[13] = w[12];                                // r r
 }
 
 template <int G, int T>
@@ -114,6 +142,8 @@ __global__ void __launch_bounds__(256, 2) fit3_kernel(Fit2Args a)
     int64_t next = 0, end = 0;   // the warp's current task [next, end)
     int64_t f = -1, fr = -1;     // task index and row of the frame being fit
     int64_t fn = -1, frn = -1;   // the group's next frame (its copy in flight)
+    float pn[4] = {0.f, 1.f, 0.f, 0.f};   // its starting point, loaded when claimed
+    int flagn = 0;
     int cs = 0;                  // slot parity of the current frame
     int oc = 0, on = 0;          // offset of tooth 0 in the current / next slot
     uint32_t ph = 0;             // phase parity of the group's two slot barriers
@@ -140,12 +170,11 @@ __global__ void __launch_bounds__(256, 2) fit3_kernel(Fit2Args a)
             oc = on;
             fn = frn = -1;
             fresh = true;
-            const float* q = a.p0 + fr * 4;
-            p[0] = (q[0] - a.x_mid) * inv_scale;
-            p[1] = q[1] * inv_scale;
-            p[2] = q[2];
-            p[3] = q[3];
-            flag = a.flags_in ? (a.flags_in[fr] & kInitFlat) : 0;
+            p[0] = (pn[0] - a.x_mid) * inv_scale;
+            p[1] = pn[1] * inv_scale;
+            p[2] = pn[2];
+            p[3] = pn[3];
+            flag = flagn;
             lambda = a.lambda0;
             it = 0;
             st = kMaxIter;
@@ -172,6 +201,13 @@ __global__ void __launch_bounds__(256, 2) fit3_kernel(Fit2Args a)
             if (((need >> leader_lane) & 1u) && rank < take) {
                 fn = next + rank;
                 frn = a.list ? static_cast<int64_t>(a.list[fn]) : fn;
+                // (params rows need only 4-byte alignment: scalar loads)
+                const float* q = a.p0 + frn * 4;
+                pn[0] = q[0];
+                pn[1] = q[1];
+                pn[2] = q[2];
+                pn[3] = q[3];
+                flagn = a.flags_in ? (a.flags_in[frn] & kInitFlat) : 0;
                 const float* src = src_base + frn * T;
                 const uintptr_t ad = reinterpret_cast<uintptr_t>(src);
                 const uintptr_t a16 = ad & ~static_cast<uintptr_t>(15);
@@ -215,13 +251,14 @@ __global__ void __launch_bounds__(256, 2) fit3_kernel(Fit2Args a)
         }
         // ---- sums at the trial point over the lane's tooth pairs ----
         const float* row = slots + (grp + S::kGroups * cs) * S::kRS + oc;
-        const float2 cc = dup2(pe[0]);
-        const float2 g2 = dup2(pe[1] * pe[1]);
+        // (any fixed 1/g is a consistent width for the model below)
+        const float igs = rcp_fast(pe[1]);
+        const float2 ig = dup2(igs);
+        const float2 ncig = dup2(-pe[0] * igs);
+        const float2 one = dup2(1.0f);
         const float2 nA = dup2(-pe[2]);
-        const float2 Bv = dup2(pe[3]);
-        float2 s[14];
-#pragma unroll
-        for (int i = 0; i < 14; ++i) s[i] = make_float2(0.f, 0.f);
+        const float2 nB = dup2(-pe[3]);
+        float2 s[13];
 #pragma unroll
         for (int j = 0; j < S::kPPL; ++j) {
             const int i = gl + G * j;
@@ -234,45 +271,60 @@ __global__ void __launch_bounds__(256, 2) fit3_kernel(Fit2Args a)
                 yv = make_float2(wlast.x != 0.f ? yv.x : 0.f, wlast.y != 0.f ? yv.y : 0.f);
             }
             yv = mul2_rounded(yv, make_float2(tb.z, tb.w));
-            const float2 d = add2(make_float2(tb.x, tb.y), make_float2(-cc.x, -cc.y));
-            const float2 D = fma2(d, d, g2);
-            const float2 q = make_float2(rcp_fast(D.x), rcp_fast(D.y));
-            float2 L = mul2(g2, q);
+            const float2 e = fma2(make_float2(tb.x, tb.y), ig, ncig);
+            const float2 E = fma2(e, e, one);
+            float2 L = make_float2(rcp_fast(E.x), rcp_fast(E.y));
             // (y - B) is exact while y and B agree within a factor of two
-            const float2 yb = add2(yv, make_float2(-Bv.x, -Bv.y));
+            const float2 yb = add2(yv, nB);
             float2 r = fma2(nA, L, yb);
-            const float2 t = mul2(L, q);
-            float2 jc = mul2(t, d);
-            float2 jg = mul2(jc, d);
+            float2 L2 = mul2(L, L);
+            float2 jc = mul2(L2, e);   // g x the centre column's L q d
             if (j == S::kPPL - 1) {
                 L = mul2(L, wlast);
+                L2 = mul2(L2, wlast);
                 jc = mul2(jc, wlast);
-                jg = mul2(jg, wlast);
                 r = mul2(r, wlast);
             }
-            s[0] = fma2(L, L, s[0]);
-            s[1] = fma2(L, jc, s[1]);
-            s[2] = fma2(L, jg, s[2]);
-            s[3] = add2(s[3], L);
-            s[4] = fma2(jc, jc, s[4]);
-            s[5] = fma2(jc, jg, s[5]);
-            s[6] = add2(s[6], jc);
-            s[7] = fma2(jg, jg, s[7]);
-            s[8] = add2(s[8], jg);
-            s[9] = fma2(L, r, s[9]);
-            s[10] = fma2(jc, r, s[10]);
-            s[11] = fma2(jg, r, s[11]);
-            s[12] = add2(s[12], r);
-            s[13] = fma2(r, r, s[13]);
+            if (j == 0) {   // the first pair starts the sums (no zeroing)
+                s[0] = L2;
+                s[1] = mul2(L2, L);
+                s[2] = mul2(L2, L2);
+                s[3] = L;
+                s[4] = mul2(L, jc);
+                s[5] = mul2(L2, jc);
+                s[6] = mul2(jc, jc);
+                s[7] = jc;
+                s[8] = mul2(L, r);
+                s[9] = mul2(jc, r);
+                s[10] = mul2(L2, r);
+                s[11] = r;
+                s[12] = mul2(r, r);
+            } else {
+                s[0] = add2(s[0], L2);
+                s[1] = fma2(L2, L, s[1]);
+                s[2] = fma2(L2, L2, s[2]);
+                s[3] = add2(s[3], L);
+                s[4] = fma2(L, jc, s[4]);
+                s[5] = fma2(L2, jc, s[5]);
+                s[6] = fma2(jc, jc, s[6]);
+                s[7] = add2(s[7], jc);
+                s[8] = fma2(L, r, s[8]);
+                s[9] = fma2(jc, r, s[9]);
+                s[10] = fma2(L2, r, s[10]);
+                s[11] = add2(s[11], r);
+                s[12] = fma2(r, r, s[12]);
+            }
         }
-        LmSums Sm;
+        float w13[13];
 #pragma unroll
-        for (int i = 0; i < 14; ++i) Sm.v[i] = s[i].x + s[i].y;
+        for (int i = 0; i < 13; ++i) w13[i] = s[i].x + s[i].y;
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
 #pragma unroll
-            for (int i = 0; i < 14; ++i) Sm.v[i] += __shfl_xor_sync(kFull, Sm.v[i], o);
+            for (int i = 0; i < 13; ++i) w13[i] += __shfl_xor_sync(kFull, w13[i], o);
         }
+        LmSums Sm;
+        sums_from_powers(w13, igs, Sm);
         // ---- LM bookkeeping (as fit2_kernel) ----
         if (f >= 0 && !done) {
             const float chi2t = Sm.v[13];
