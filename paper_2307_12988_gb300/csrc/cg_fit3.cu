@@ -31,6 +31,15 @@
 //    L, L jc', L^2 jc', jc'^2, jc', L r, jc' r, L^2 r, r, r^2 with
 //    jc' = L^2 e (13 instead of 14, and no separate L q product); the 14
 //    sums of the textbook normal equations follow from them per frame.
+//
+// MODEL 1 is the paper's Fano profile (centre free, scale A and offset B
+// boxed, asymmetry q and width g fixed; an active set holds a bound
+// parameter whose gradient points out of its box, and the trial point is
+// clamped onto the box), as fit2_kernel<G, PPL, EXACT, 1>: per point
+// F = (q + e)^2 / (1 + e^2) and jc' = (q + e)(1 - q e) / (1 + e^2)^2, the
+// centre column being -2 A jc' / g; 9 sums (jc' jc', jc' F, jc', F F, F,
+// jc' r, F r, r, r r).  Its starting centre is the given one (the median
+// filter's) or the lowest tooth of the frame (first on ties) moved by q g.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -89,9 +98,10 @@ struct Fit3Shape {
     static constexpr int kSlots = 2 * kGroups;                  // per warp
 };
 
-template <int G, int T>
+template <int G, int T, int MODEL>
 __global__ void __launch_bounds__(256, 2) fit3_kernel(Fit2Args a)
 {
+    constexpr int kW = MODEL == 1 ? 9 : 13;   // sums per point
     using S = Fit3Shape<G, T>;
     extern __shared__ __align__(16) float4 f3sm[];
     float4* tab = f3sm;
@@ -170,11 +180,54 @@ __global__ void __launch_bounds__(256, 2) fit3_kernel(Fit2Args a)
             oc = on;
             fn = frn = -1;
             fresh = true;
-            p[0] = (pn[0] - a.x_mid) * inv_scale;
-            p[1] = pn[1] * inv_scale;
-            p[2] = pn[2];
-            p[3] = pn[3];
-            flag = flagn;
+            if constexpr (MODEL == 1) {
+                float c0;
+                if (a.p0) {
+                    c0 = (pn[0] - a.x_mid) * inv_scale;
+                } else {
+                    // the lowest tooth of the normalised spectrum (first on
+                    // ties), the group's lanes scanning their pairs
+                    const float* row = slots + (grp + S::kGroups * cs) * S::kRS + oc;
+                    float best = INFINITY;
+                    int bk = 0x7fffffff;
+#pragma unroll 4
+                    for (int j = 0; j < S::kPPL; ++j) {
+                        const int i = gl + G * j;
+                        const float4 tb = tab[i];
+                        if (2 * i < T) {
+                            const float v = __fmul_rn(row[2 * i], tb.z);
+                            if (v < best) { best = v; bk = 2 * i; }
+                        }
+                        if (2 * i + 1 < T) {
+                            const float v = __fmul_rn(row[2 * i + 1], tb.w);
+                            if (v < best) { best = v; bk = 2 * i + 1; }
+                        }
+                    }
+                    // (only the starting groups are here: shuffle within the group)
+                    const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << leader_lane);
+#pragma unroll
+                    for (int o = G / 2; o > 0; o >>= 1) {
+                        const float ob = __shfl_xor_sync(gmask, best, o);
+                        const int ok = __shfl_xor_sync(gmask, bk, o);
+                        if (ob < best || (ob == best && ok < bk)) {
+                            best = ob;
+                            bk = ok;
+                        }
+                    }
+                    c0 = (bk < T ? a.u[bk] : 0.f) + a.fano_shift;
+                }
+                p[0] = c0;
+                p[1] = a.fano_g;
+                p[2] = fminf(fmaxf(a.fano_A0, a.fano_Alo), a.fano_Ahi);
+                p[3] = fminf(fmaxf(a.fano_B0, a.fano_Blo), a.fano_Bhi);
+                flag = 0;
+            } else {
+                p[0] = (pn[0] - a.x_mid) * inv_scale;
+                p[1] = pn[1] * inv_scale;
+                p[2] = pn[2];
+                p[3] = pn[3];
+                flag = flagn;
+            }
             lambda = a.lambda0;
             it = 0;
             st = kMaxIter;
@@ -202,11 +255,13 @@ __global__ void __launch_bounds__(256, 2) fit3_kernel(Fit2Args a)
                 fn = next + rank;
                 frn = a.list ? static_cast<int64_t>(a.list[fn]) : fn;
                 // (params rows need only 4-byte alignment: scalar loads)
-                const float* q = a.p0 + frn * 4;
-                pn[0] = q[0];
-                pn[1] = q[1];
-                pn[2] = q[2];
-                pn[3] = q[3];
+                if (a.p0) {
+                    const float* q = a.p0 + frn * 4;
+                    pn[0] = q[0];
+                    pn[1] = q[1];
+                    pn[2] = q[2];
+                    pn[3] = q[3];
+                }
                 flagn = a.flags_in ? (a.flags_in[frn] & kInitFlat) : 0;
                 const float* src = src_base + frn * T;
                 const uintptr_t ad = reinterpret_cast<uintptr_t>(src);
@@ -240,92 +295,184 @@ __global__ void __launch_bounds__(256, 2) fit3_kernel(Fit2Args a)
         bool done = false;
         const bool trial = f >= 0 && !fresh;
         if (trial) {
-            float delta[4] = {0.f, 0.f, 0.f, 0.f};
-            if (lm_solve4_fast(Nm, lambda, delta)) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) pe[i] = p[i] + delta[i];
+            if constexpr (MODEL == 1) {
+                // a scale or offset on its bound with the gradient pointing
+                // outward is held for this step (active set); c steps freely,
+                // A and B are clamped onto their boxes
+                int held = 0;
+                if ((p[2] <= a.fano_Alo && Nm.b[1] < 0.f) || (p[2] >= a.fano_Ahi && Nm.b[1] > 0.f)) held |= 2;
+                if ((p[3] <= a.fano_Blo && Nm.b[2] < 0.f) || (p[3] >= a.fano_Bhi && Nm.b[2] > 0.f)) held |= 4;
+                float d3[3] = {0.f, 0.f, 0.f};
+                if (lm_solve3<float>(Nm, lambda, held, d3)) {
+                    pe[0] = p[0] + d3[0];
+                    pe[2] = fminf(fmaxf(p[2] + d3[1], a.fano_Alo), a.fano_Ahi);
+                    pe[3] = fminf(fmaxf(p[3] + d3[2], a.fano_Blo), a.fano_Bhi);
+                } else {
+                    st = kSingular;
+                    done = true;
+                }
             } else {
-                st = kSingular;
-                done = true;
+                float delta[4] = {0.f, 0.f, 0.f, 0.f};
+                if (lm_solve4_fast(Nm, lambda, delta)) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) pe[i] = p[i] + delta[i];
+                } else {
+                    st = kSingular;
+                    done = true;
+                }
             }
         }
         // ---- sums at the trial point over the lane's tooth pairs ----
         const float* row = slots + (grp + S::kGroups * cs) * S::kRS + oc;
         // (any fixed 1/g is a consistent width for the model below)
-        const float igs = rcp_fast(pe[1]);
+        const float igs = MODEL == 1 ? a.fano_inv_g : rcp_fast(pe[1]);
         const float2 ig = dup2(igs);
         const float2 ncig = dup2(-pe[0] * igs);
         const float2 one = dup2(1.0f);
         const float2 nA = dup2(-pe[2]);
         const float2 nB = dup2(-pe[3]);
-        float2 s[13];
+        float2 s[kW];
+        if constexpr (MODEL == 1) {
+            const float2 qq = dup2(a.fano_q);
+            const float2 nq = dup2(-a.fano_q);
 #pragma unroll
-        for (int j = 0; j < S::kPPL; ++j) {
-            const int i = gl + G * j;
-            const float4 tb = tab[i];
-            float2 yv;
-            if (j < S::kPPL - 1) {
-                yv = make_float2(row[2 * i], row[2 * i + 1]);
-            } else {
-                yv = make_float2(row[klast0], row[klast1]);
-                yv = make_float2(wlast.x != 0.f ? yv.x : 0.f, wlast.y != 0.f ? yv.y : 0.f);
+            for (int j = 0; j < S::kPPL; ++j) {
+                const int i = gl + G * j;
+                const float4 tb = tab[i];
+                float2 yv;
+                if (j < S::kPPL - 1) {
+                    yv = make_float2(row[2 * i], row[2 * i + 1]);
+                } else {
+                    yv = make_float2(row[klast0], row[klast1]);
+                    yv = make_float2(wlast.x != 0.f ? yv.x : 0.f, wlast.y != 0.f ? yv.y : 0.f);
+                }
+                yv = mul2_rounded(yv, make_float2(tb.z, tb.w));
+                const float2 e = fma2(make_float2(tb.x, tb.y), ig, ncig);
+                const float2 E = fma2(e, e, one);
+                const float2 id = make_float2(rcp_fast(E.x), rcp_fast(E.y));
+                const float2 qe = add2(e, qq);
+                float2 F = mul2(mul2(qe, qe), id);
+                const float2 yb = add2(yv, nB);
+                float2 r = fma2(nA, F, yb);
+                // (q + e)(1 - q e) / (1 + e^2)^2: -g / (2 A) x the centre column
+                float2 jc = mul2(mul2(qe, fma2(nq, e, one)), mul2(id, id));
+                if (j == S::kPPL - 1) {
+                    F = mul2(F, wlast);
+                    jc = mul2(jc, wlast);
+                    r = mul2(r, wlast);
+                }
+                if (j == 0) {
+                    s[0] = mul2(jc, jc);
+                    s[1] = mul2(jc, F);
+                    s[2] = jc;
+                    s[3] = mul2(F, F);
+                    s[4] = F;
+                    s[5] = mul2(jc, r);
+                    s[6] = mul2(F, r);
+                    s[7] = r;
+                    s[8] = mul2(r, r);
+                } else {
+                    s[0] = fma2(jc, jc, s[0]);
+                    s[1] = fma2(jc, F, s[1]);
+                    s[2] = add2(s[2], jc);
+                    s[3] = fma2(F, F, s[3]);
+                    s[4] = add2(s[4], F);
+                    s[5] = fma2(jc, r, s[5]);
+                    s[6] = fma2(F, r, s[6]);
+                    s[7] = add2(s[7], r);
+                    s[8] = fma2(r, r, s[8]);
+                }
             }
-            yv = mul2_rounded(yv, make_float2(tb.z, tb.w));
-            const float2 e = fma2(make_float2(tb.x, tb.y), ig, ncig);
-            const float2 E = fma2(e, e, one);
-            float2 L = make_float2(rcp_fast(E.x), rcp_fast(E.y));
-            // (y - B) is exact while y and B agree within a factor of two
-            const float2 yb = add2(yv, nB);
-            float2 r = fma2(nA, L, yb);
-            float2 L2 = mul2(L, L);
-            float2 jc = mul2(L2, e);   // g x the centre column's L q d
-            if (j == S::kPPL - 1) {
-                L = mul2(L, wlast);
-                L2 = mul2(L2, wlast);
-                jc = mul2(jc, wlast);
-                r = mul2(r, wlast);
-            }
-            if (j == 0) {   // the first pair starts the sums (no zeroing)
-                s[0] = L2;
-                s[1] = mul2(L2, L);
-                s[2] = mul2(L2, L2);
-                s[3] = L;
-                s[4] = mul2(L, jc);
-                s[5] = mul2(L2, jc);
-                s[6] = mul2(jc, jc);
-                s[7] = jc;
-                s[8] = mul2(L, r);
-                s[9] = mul2(jc, r);
-                s[10] = mul2(L2, r);
-                s[11] = r;
-                s[12] = mul2(r, r);
-            } else {
-                s[0] = add2(s[0], L2);
-                s[1] = fma2(L2, L, s[1]);
-                s[2] = fma2(L2, L2, s[2]);
-                s[3] = add2(s[3], L);
-                s[4] = fma2(L, jc, s[4]);
-                s[5] = fma2(L2, jc, s[5]);
-                s[6] = fma2(jc, jc, s[6]);
-                s[7] = add2(s[7], jc);
-                s[8] = fma2(L, r, s[8]);
-                s[9] = fma2(jc, r, s[9]);
-                s[10] = fma2(L2, r, s[10]);
-                s[11] = add2(s[11], r);
-                s[12] = fma2(r, r, s[12]);
+        } else {
+    #pragma unroll
+            for (int j = 0; j < S::kPPL; ++j) {
+                const int i = gl + G * j;
+                const float4 tb = tab[i];
+                float2 yv;
+                if (j < S::kPPL - 1) {
+                    yv = make_float2(row[2 * i], row[2 * i + 1]);
+                } else {
+                    yv = make_float2(row[klast0], row[klast1]);
+                    yv = make_float2(wlast.x != 0.f ? yv.x : 0.f, wlast.y != 0.f ? yv.y : 0.f);
+                }
+                yv = mul2_rounded(yv, make_float2(tb.z, tb.w));
+                const float2 e = fma2(make_float2(tb.x, tb.y), ig, ncig);
+                const float2 E = fma2(e, e, one);
+                float2 L = make_float2(rcp_fast(E.x), rcp_fast(E.y));
+                // (y - B) is exact while y and B agree within a factor of two
+                const float2 yb = add2(yv, nB);
+                float2 r = fma2(nA, L, yb);
+                float2 L2 = mul2(L, L);
+                float2 jc = mul2(L2, e);   // g x the centre column's L q d
+                if (j == S::kPPL - 1) {
+                    L = mul2(L, wlast);
+                    L2 = mul2(L2, wlast);
+                    jc = mul2(jc, wlast);
+                    r = mul2(r, wlast);
+                }
+                if (j == 0) {   // the first pair starts the sums (no zeroing)
+                    s[0] = L2;
+                    s[1] = mul2(L2, L);
+                    s[2] = mul2(L2, L2);
+                    s[3] = L;
+                    s[4] = mul2(L, jc);
+                    s[5] = mul2(L2, jc);
+                    s[6] = mul2(jc, jc);
+                    s[7] = jc;
+                    s[8] = mul2(L, r);
+                    s[9] = mul2(jc, r);
+                    s[10] = mul2(L2, r);
+                    s[11] = r;
+                    s[12] = mul2(r, r);
+                } else {
+                    s[0] = add2(s[0], L2);
+                    s[1] = fma2(L2, L, s[1]);
+                    s[2] = fma2(L2, L2, s[2]);
+                    s[3] = add2(s[3], L);
+                    s[4] = fma2(L, jc, s[4]);
+                    s[5] = fma2(L2, jc, s[5]);
+                    s[6] = fma2(jc, jc, s[6]);
+                    s[7] = add2(s[7], jc);
+                    s[8] = fma2(L, r, s[8]);
+                    s[9] = fma2(jc, r, s[9]);
+                    s[10] = fma2(L2, r, s[10]);
+                    s[11] = add2(s[11], r);
+                    s[12] = fma2(r, r, s[12]);
+                }
             }
         }
-        float w13[13];
+        float w[kW];
 #pragma unroll
-        for (int i = 0; i < 13; ++i) w13[i] = s[i].x + s[i].y;
+        for (int i = 0; i < kW; ++i) w[i] = s[i].x + s[i].y;
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
 #pragma unroll
-            for (int i = 0; i < 13; ++i) w13[i] += __shfl_xor_sync(kFull, w13[i], o);
+            for (int i = 0; i < kW; ++i) w[i] += __shfl_xor_sync(kFull, w[i], o);
         }
-        LmSums Sm;
-        sums_from_powers(w13, igs, Sm);
         // ---- LM bookkeeping (as fit2_kernel) ----
+        // the sums of the normal equations (and chi^2 in v[13])
+        LmSums Sm;
+        if constexpr (MODEL == 1) {
+            // the centre column is kappa jc' with kappa = -2 A / g
+            const float ka = -2.0f * pe[2] * igs;
+            Sm.v[0] = w[0] * (ka * ka);
+            Sm.v[1] = w[1] * ka;
+            Sm.v[2] = w[2] * ka;
+            Sm.v[3] = w[3];
+            Sm.v[4] = w[4];
+            Sm.v[5] = w[5] * ka;
+            Sm.v[6] = w[6];
+            Sm.v[7] = w[7];
+            Sm.v[13] = w[8];
+        } else {
+            sums_from_powers(w, igs, Sm);
+        }
+        auto normal = [&](Normal& N) {
+            if constexpr (MODEL == 1)
+                make_normal_fano(Sm, T, N);
+            else
+                make_normal_fast(Sm, pe[1], pe[2], T, N);
+        };
         if (f >= 0 && !done) {
             const float chi2t = Sm.v[13];
             if (fresh) {
@@ -334,7 +481,7 @@ __global__ void __launch_bounds__(256, 2) fit3_kernel(Fit2Args a)
                     st = kNonfinite;
                     done = true;
                 } else {
-                    make_normal_fast(Sm, pe[1], pe[2], T, Nm);
+                    normal(Nm);
                     if (a.max_iter <= 0) done = true;
                 }
             } else {
@@ -353,7 +500,7 @@ __global__ void __launch_bounds__(256, 2) fit3_kernel(Fit2Args a)
 #pragma unroll
                     for (int i = 0; i < 4; ++i) p[i] = pe[i];
                     chi2 = chi2t;
-                    make_normal_fast(Sm, pe[1], pe[2], T, Nm);
+                    normal(Nm);
                     lambda *= 0.1f;
                 } else {
                     lambda *= 10.0f;
@@ -387,10 +534,10 @@ __global__ void __launch_bounds__(256, 2) fit3_kernel(Fit2Args a)
     if (failed && lane == 0 && a.err) atomicExch(a.err, 4);
 }
 
-template <int G, int T>
+template <int G, int T, int MODEL>
 void* fit3_fn()
 {
-    return reinterpret_cast<void*>(&fit3_kernel<G, T>);
+    return reinterpret_cast<void*>(&fit3_kernel<G, T, MODEL>);
 }
 
 template <int G, int T>
@@ -401,23 +548,25 @@ size_t fit3_bytes(int warps)
 }
 
 struct Fit3Inst {
-    int G, T;
+    int G, T, model;
     void* (*fn)();
     size_t (*bytes)(int);
 };
 // the workload geometries: 21 teeth (one lane per frame), 99 (two lanes),
 // 201 and 221 (four lanes)
+// (the Fano profile at the paper's 99 teeth)
 const Fit3Inst kFit3[] = {
-    {1, 21, fit3_fn<1, 21>, fit3_bytes<1, 21>},
-    {2, 99, fit3_fn<2, 99>, fit3_bytes<2, 99>},
-    {4, 201, fit3_fn<4, 201>, fit3_bytes<4, 201>},
-    {4, 221, fit3_fn<4, 221>, fit3_bytes<4, 221>},
+    {1, 21, 0, fit3_fn<1, 21, 0>, fit3_bytes<1, 21>},
+    {2, 99, 0, fit3_fn<2, 99, 0>, fit3_bytes<2, 99>},
+    {4, 201, 0, fit3_fn<4, 201, 0>, fit3_bytes<4, 201>},
+    {4, 221, 0, fit3_fn<4, 221, 0>, fit3_bytes<4, 221>},
+    {2, 99, 1, fit3_fn<2, 99, 1>, fit3_bytes<2, 99>},
 };
 
-const Fit3Inst* fit3_find(int T)
+const Fit3Inst* fit3_find(int T, int model)
 {
     for (const Fit3Inst& f : kFit3)
-        if (f.T == T) return &f;
+        if (f.T == T && f.model == model) return &f;
     return nullptr;
 }
 
@@ -429,7 +578,7 @@ const Fit3Inst* fit3_find(int T)
 cudaError_t setup_fit3(cg_plan_s* p)
 {
     p->fit3_ok = false;
-    const Fit3Inst* fi = fit3_find(p->T);
+    const Fit3Inst* fi = fit3_find(p->T, p->opts.model);
     if (!fi) return cudaSuccess;
     int smem_sm = 0, smem_block = 0;
     cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
@@ -456,7 +605,7 @@ cudaError_t setup_fit3(cg_plan_s* p)
 
 cudaError_t launch_fit3(const cg_plan_s* p, Fit2Args a, cudaStream_t s)
 {
-    const Fit3Inst* fi = fit3_find(p->T);
+    const Fit3Inst* fi = fit3_find(p->T, p->opts.model);
     if (!fi || !p->fit3_ok) return cudaErrorInvalidValue;
     const int gpw = 32 / fi->G;   // groups per warp
     a.task = 2 * gpw;

@@ -65,9 +65,10 @@ static_assert(kItems * kFoldWarps * 32 == kFM * (kFK / 4), "fold items must cove
 // bounded wait (kPolls polls)
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag)
 {
+    const uint64_t t0 = tc::globaltimer_ns();
     for (uint32_t i = 0; i < kPolls; ++i) {
         if (tc::mbar_try_wait(bar, parity)) return true;
-        if ((i & 1023u) == 1023u && *abort_flag) return false;
+        if ((i & 255u) == 255u && (*abort_flag || tc::globaltimer_ns() - t0 > tc::kWaitLimitNs)) return false;
     }
     return false;
 }

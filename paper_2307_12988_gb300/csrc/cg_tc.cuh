@@ -46,12 +46,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Wait for the phase of the given parity; gives up after max_iters polls and
-// returns false (the caller records the error and unwinds).
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Longest any bounded wait of the library lasts.  A single try_wait may
+// suspend the thread for a hardware-defined time, so a bound on the number of
+// polls alone does not bound the time; every wait also checks the clock.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+// Wait for the phase of the given parity; gives up after max_iters polls or
+// kWaitLimitNs and returns false (the caller records the error and unwinds).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_iters)
 {
-    for (uint32_t i = 0; i < max_iters; ++i)
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 0; i < max_iters; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    }
     return false;
 }
 
