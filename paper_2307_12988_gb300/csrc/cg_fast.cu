@@ -27,6 +27,7 @@
 #include "cg_fft.cuh"
 #include "cg_fit.cuh"
 #include "cg_internal.h"
+#include "cg_net.cuh"
 #include "cg_stage.cuh"
 #include "cg_tc.cuh"
 
@@ -178,37 +179,6 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
 // ---------------------------------------------------------------------------
 // moment initial guess, one lane per frame
 // ---------------------------------------------------------------------------
-// Comparator list of Batcher's odd-even merge sort on N = 2^m values
-// (Knuth, TAOCP vol. 3, 5.3.4), built at compile time.
-template <int N>
-struct OddEvenNet {
-    static constexpr int count_()
-    {
-        int c = 0;
-        for (int p = 1; p < N; p <<= 1)
-            for (int k = p; k >= 1; k >>= 1)
-                for (int j = k % p; j + k < N; j += 2 * k)
-                    for (int i = 0; i < k && i + j + k < N; ++i)
-                        if ((i + j) / (2 * p) == (i + j + k) / (2 * p)) ++c;
-        return c;
-    }
-    static constexpr int kCount = count_();
-    int lo[kCount], hi[kCount];
-    constexpr OddEvenNet() : lo(), hi()
-    {
-        int c = 0;
-        for (int p = 1; p < N; p <<= 1)
-            for (int k = p; k >= 1; k >>= 1)
-                for (int j = k % p; j + k < N; j += 2 * k)
-                    for (int i = 0; i < k && i + j + k < N; ++i)
-                        if ((i + j) / (2 * p) == (i + j + k) / (2 * p)) {
-                            lo[c] = i + j;
-                            hi[c] = i + j + k;
-                            ++c;
-                        }
-    }
-};
-
 // Moment initial guess from the baseline B0 (the median of the outer teeth):
 // d = y - B0, s = sign of the largest |d|, w = max(s d, 0); c0 = centroid of
 // w over the abscissa, A0 = s max w, g0 = area / (pi |A0|) clamped to

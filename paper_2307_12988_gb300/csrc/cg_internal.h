@@ -189,7 +189,7 @@ struct MedianArgs {
     float* params;           // [n][4]: c0 into column 0
     int64_t n;
     int T, S, R;             // teeth, shared row stride ((T + 6) | 1), rows per block
-    int sm_key, sm_total;    // shared-memory layout
+    int sm_key, sm_raw, sm_total;   // shared-memory layout
 };
 
 struct DevTables {

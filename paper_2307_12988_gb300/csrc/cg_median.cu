@@ -19,9 +19,10 @@
 //      smallest column median, at most 21 above the largest); windows with
 //      L(k) <= min_k U(k) are candidates (about 12 of 99 at the paper rate);
 //   4. the exact median t of the window of least U (sort its 7 columns, then
-//      its 7 rows -- the matrix stays sorted both ways --, drop the 10
-//      elements with more than 25 elements above or below them by position,
-//      select the 15th smallest of the 29 left by forgetful selection);
+//      its 7 rows -- the matrix stays sorted both ways --, drop the 20
+//      elements with 25 or more elements certainly above or below them by
+//      position, select the 15th smallest of the 29 left with a merge
+//      network pruned to that output);
 //   5. every candidate is compared with t by counting its values below and
 //      at or below t: a median below t (rare) is computed exactly and
 //      competes by a 64-bit (value, tooth) atomicMin, a median equal to t
@@ -34,6 +35,8 @@
 #include <cuda_runtime.h>
 
 #include "cg_internal.h"
+#include "cg_net.cuh"
+#include "cg_stage.cuh"
 
 namespace cg {
 
@@ -72,28 +75,6 @@ __device__ __forceinline__ float median7(float (&v)[7])
     v[2] = fmaxf(v[1], v[2]); v[4] = fminf(v[4], v[6]);
     v[3] = fmaxf(v[2], v[3]); v[4] = fminf(v[4], v[5]);
     return fminf(v[3], v[4]);
-}
-
-// median of N = 2M + 1 values by forgetful selection: the buffer v[t .. M+2)
-// loses its minimum (to v[t]) and maximum (to v[M+1]) each step and takes the
-// next input into v[M+1]; fully unrolled, so v stays in registers
-template <int N>
-__device__ __forceinline__ float forgetful_median(float (&v)[N])
-{
-    constexpr int M = N / 2;
-#pragma unroll
-    for (int t = 0; t < M - 1; ++t) {
-        const int b = M + 2 - t;
-#pragma unroll
-        for (int i = 1; i < b; ++i) cmpx(v[t], v[t + i]);
-#pragma unroll
-        for (int i = 1; i < b - 1; ++i) cmpx(v[t + i], v[M + 1]);
-        v[M + 1] = v[M + 2 + t];
-    }
-    cmpx(v[M - 1], v[M]);
-    cmpx(v[M], v[M + 1]);
-    cmpx(v[M - 1], v[M]);
-    return v[M];
 }
 
 // mirrored index for i in [-3, n + 3): reflections until it lies in [0, n)
@@ -139,17 +120,23 @@ __device__ __forceinline__ float window_median(const float* tile, int S, int r, 
 #pragma unroll
         for (int c = 0; c < 7; ++c) m[c][j] = row[c];
     }
-    // positions (j, c) with at most 24 elements certainly below and above
-    float v[29];
+    // positions (j, c) with at most 24 elements certainly below and above;
+    // the 15th smallest of these 29 by the rank-pruned merge network (depth
+    // <= 15, where a forgetful selection is a chain of ~440 dependent steps)
+    float v[32];
     int q = 0;
 #pragma unroll
     for (int j = 0; j < 7; ++j)
 #pragma unroll
         for (int c = 0; c < 7; ++c)
             if ((j + 1) * (c + 1) <= 25 && (7 - j) * (7 - c) <= 25) v[q++] = m[c][j];
-    return forgetful_median<29>(v);
+    v[29] = v[30] = v[31] = INFINITY;
+    return rank_select<32, 29, 14>(v);
 }
 
+// KPL: windows per lane in the bounds pass (T <= 32 KPL), a compile-time
+// count so that no unrolled step runs past the row
+template <int KPL>
 __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
 {
     extern __shared__ __align__(16) unsigned char msm[];
@@ -164,19 +151,55 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
     int* ka = count + 4;                                               // [R] first window of least U
     float* tq = reinterpret_cast<float*>(ka + R);                      // [R] its exact median
     int* tie = reinterpret_cast<int*>(tq + R);                         // [R] first window with median = tq
+    int* mir = tie + R;                                                // [W] tooth of padded column j
+    float* iref = reinterpret_cast<float*>(mir + W);                   // [T] 1 / reference
+    float* raw = reinterpret_cast<float*>(msm + a.sm_raw);             // [(R + 6) T + 4] staged rows
+    const float* src = a.y ? a.y : a.amps;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kMedThreads / 32;
+    for (int j = tid; j < W; j += kMedThreads) mir[j] = mirror(j - 3, T);
+    for (int k = tid; k < T; k += kMedThreads) iref[k] = a.y ? 1.0f : a.inv_ref[k];
+    // the rows a block needs, [rlo, rhi): its own and 3 on either side, within
+    // the image (mirrored rows are among them); staged by asynchronous 16-byte
+    // copies, the next block's while the current one is filtered
+    auto row_range = [&](int64_t bb, int64_t& rlo, int64_t& rhi) {
+        const int64_t j0 = bb * R;
+        const int64_t j1 = j0 + R < n ? j0 + R : n;
+        rlo = j0 - 3 > 0 ? j0 - 3 : 0;
+        rhi = j1 + 3 < n ? j1 + 3 : n;
+    };
+    int off = 0;
+    if (static_cast<int64_t>(blockIdx.x) * R < n) {
+        int64_t rlo, rhi;
+        row_range(blockIdx.x, rlo, rhi);
+        off = stage_async(src, rlo * T, (rhi - rlo) * T, raw);
+    }
+    __syncthreads();
     for (int64_t b = blockIdx.x; b * R < n; b += gridDim.x) {
         const int64_t i0 = b * R;
         const int rows = static_cast<int>((n - i0) < R ? (n - i0) : R);
-        // 1. the tile: rows i0 - 3 .. i0 + rows + 2 and teeth -3 .. T + 2, mirrored
+        int64_t rlo, rhi;
+        row_range(b, rlo, rhi);
+        cp_async_wait_all();
+        __syncthreads();
+        // 1. the tile: rows i0 - 3 .. i0 + rows + 2 and teeth -3 .. T + 2,
+        //    mirrored, normalised (x 1 when y is given: exact)
         for (int t = warp; t < rows + 6; t += kWarps) {
-            const int64_t row = mirror64(i0 - 3 + t, n);
-            const float* src = a.y ? a.y + row * T : a.amps + row * T;
+            const float* rr = raw + off + (mirror64(i0 - 3 + t, n) - rlo) * T;
             for (int j = lane; j < W; j += 32) {
-                const int k = mirror(j - 3, T);
-                tile[t * S + j] = a.y ? src[k] : __fmul_rn(src[k], a.inv_ref[k]);
+                const int k = mir[j];
+                tile[t * S + j] = __fmul_rn(rr[k], iref[k]);
+            }
+        }
+        __syncthreads();
+        // the staged rows are in the tile: the next block's rows go to raw
+        {
+            const int64_t bn = b + gridDim.x;
+            if (bn * R < n) {
+                int64_t nlo, nhi;
+                row_range(bn, nlo, nhi);
+                off = stage_async(src, nlo * T, (nhi - nlo) * T, raw);
             }
         }
         if (tid < R) {
@@ -185,23 +208,35 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
         }
         if (tid == 0) *count = 0;
         __syncthreads();
-        // 2. medians of the 7-row column segments
-        for (int r = warp; r < rows; r += kWarps)
-            for (int j = lane; j < W; j += 32) {
-                float v[7];
+        // 2. medians of the 7-row column segments: one thread per column and
+        //    16 consecutive rows loads the column's 22 values once
+        for (int idx = tid; idx < W * ((rows + 15) / 16); idx += kMedThreads) {
+            const int h = idx / W;
+            const int j = idx - h * W;
+            const int r0 = 16 * h;
+            const int nr = rows - r0 < 16 ? rows - r0 : 16;
+            float col[22];
 #pragma unroll
-                for (int q = 0; q < 7; ++q) v[q] = tile[(r + q) * S + j];
-                cm[r * S + j] = median7(v);
+            for (int q = 0; q < 22; ++q) col[q] = q < nr + 6 ? tile[(r0 + q) * S + j] : 0.f;
+#pragma unroll
+            for (int rr = 0; rr < 16; ++rr) {
+                if (rr < nr) {
+                    float v[7];
+#pragma unroll
+                    for (int q = 0; q < 7; ++q) v[q] = col[rr + q];
+                    cm[(r0 + rr) * S + j] = median7(v);
+                }
             }
+        }
         __syncthreads();
         // 3. per row (one warp): bounds and the candidate windows
         for (int r = warp; r < rows; r += kWarps) {
             const float* cr = cm + r * S;
             float ustar = INFINITY;
             int kbest = 0x7fffffff;
-            float lo[kMaxKPerLane];                // L(k) of this lane's windows
+            float lo[KPL];                         // L(k) of this lane's windows
 #pragma unroll
-            for (int q = 0; q < kMaxKPerLane; ++q) {
+            for (int q = 0; q < KPL; ++q) {
                 const int k = lane + 32 * q;
                 lo[q] = INFINITY;
                 if (k < T) {
@@ -229,7 +264,7 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
             }
             if (lane == 0) ka[r] = kbest < T ? kbest : 0;
 #pragma unroll
-            for (int q = 0; q < kMaxKPerLane; ++q) {
+            for (int q = 0; q < KPL; ++q) {
                 const int k = lane + 32 * q;
                 if (32 * q >= T) break;
                 const bool cand = k < T && !(lo[q] > ustar);   // (non-finite rows keep every window)
@@ -285,6 +320,13 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
 
 }  // namespace
 
+static void* median_fn(int T)
+{
+    if (T <= 128) return reinterpret_cast<void*>(&median_init_kernel<4>);
+    if (T <= 256) return reinterpret_cast<void*>(&median_init_kernel<8>);
+    return reinterpret_cast<void*>(&median_init_kernel<kMaxKPerLane>);
+}
+
 // Rows per block (32, 16, 8 or 4: the most whose tables fit in 100 KB of
 // shared memory), the layout and the grid.
 cudaError_t setup_median(cg_plan_s* p)
@@ -301,16 +343,22 @@ cudaError_t setup_median(cg_plan_s* p)
     auto bytes = [&](int r) {
         const size_t tables = sizeof(float) * (static_cast<size_t>(r + 6) * S + static_cast<size_t>(r) * S) +
                               sizeof(int) * static_cast<size_t>(r) * T;
-        return ((tables + 15) & ~static_cast<size_t>(15)) + 8 * r + 16 + 12 * r;
+        const size_t rest = ((tables + 15) & ~static_cast<size_t>(15)) + 8 * r + 16 + 12 * r + 4 * (T + 6) + 4 * T;
+        const size_t raw = sizeof(float) * ((static_cast<size_t>(r + 6) * T + 4 + 3) & ~static_cast<size_t>(3));
+        return ((rest + 15) & ~static_cast<size_t>(15)) + raw;
     };
     while (R > 4 && bytes(R) > 100 * 1024) R /= 2;
     m.R = R;
     const size_t tables = sizeof(float) * (static_cast<size_t>(R + 6) * S + static_cast<size_t>(R) * S) +
                           sizeof(int) * static_cast<size_t>(R) * T;
     m.sm_key = static_cast<int>((tables + 15) & ~static_cast<size_t>(15));
+    {
+        const size_t rest = static_cast<size_t>(m.sm_key) + 8 * R + 16 + 12 * R + 4 * (T + 6) + 4 * T;
+        m.sm_raw = static_cast<int>((rest + 15) & ~static_cast<size_t>(15));
+    }
     m.sm_total = static_cast<int>(bytes(R));
     cudaError_t e;
-    void* fn = reinterpret_cast<void*>(&median_init_kernel);
+    void* fn = median_fn(T);
     if ((e = raise_smem_limit(fn, m.sm_total)) != cudaSuccess) return e;
     int occ = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kMedThreads, m.sm_total)) != cudaSuccess)
@@ -334,8 +382,7 @@ cudaError_t launch_median(const cg_plan_s* p, const float* y, const float* amps,
     const int64_t nb = (n + m.R - 1) / m.R;
     const int grid = static_cast<int>(nb < p->grid_median ? nb : p->grid_median);
     void* args[] = {&m};
-    return cudaLaunchKernel(reinterpret_cast<void*>(&median_init_kernel), dim3(grid), dim3(kMedThreads), args,
-                            m.sm_total, s);
+    return cudaLaunchKernel(median_fn(m.T), dim3(grid), dim3(kMedThreads), args, m.sm_total, s);
 }
 
 }  // namespace cg
