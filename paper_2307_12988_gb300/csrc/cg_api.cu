@@ -291,7 +291,7 @@ cudaError_t setup_fit_kernels(cg_plan_s* p)
         if ((e = cudaMalloc(&p->d.err, sizeof(int))) != cudaSuccess) return e;
         if ((e = cudaMemset(p->d.err, 0, sizeof(int))) != cudaSuccess) return e;
     }
-    void* fi = cg::init_ptr(npad);
+    void* fi = cg::init_ptr(npad, p->n_outer);
     if ((e = cg::raise_smem_limit(fi, p->init_smem)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fi, 128, p->init_smem)) != cudaSuccess) return e;
     if (occ < 1) return cudaSuccess;

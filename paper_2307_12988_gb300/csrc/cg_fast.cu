@@ -239,7 +239,10 @@ __device__ __forceinline__ void moment_finish(Y y, U u, int T, float B0, float u
 // then computes its frame's guess as the oracle defines it: baseline = median
 // of the outer fifth (sorted with the network, +inf padding), sign of the
 // largest deviation, centroid / extreme / area of the one-signed excess.
-template <int NPAD>
+// NOUT > 0: the outer set has NOUT teeth (a compile-time count): its median
+// comes from the merge network pruned to the two middle ranks; NOUT = 0 sorts
+// the NPAD wires (a.n_outer real, the rest +infinity) fully
+template <int NPAD, int NOUT>
 __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
 {
     extern __shared__ __align__(16) float ism[];
@@ -393,23 +396,32 @@ __global__ void __launch_bounds__(128) init_kernel(InitArgs a)
             const bool scale = in_smem_raw && !a.y;
             auto yk = [&](int k) { return scale ? __fmul_rn(r[k], iref[k]) : r[k]; };
             float v[NPAD];
+            float B0;
+            if constexpr (NOUT > 0) {
 #pragma unroll
-            for (int i = 0; i < NPAD; ++i) v[i] = (i < a.n_outer) ? yk(outer[i]) : INFINITY;
+                for (int i = 0; i < NPAD; ++i) v[i] = i < NOUT ? yk(outer[i]) : INFINITY;
+                constexpr int kLo = (NOUT - 1) / 2, kHi = NOUT / 2;
+                rank_network<NPAD, NOUT, kLo, kHi>(v);
+                B0 = 0.5f * (v[kLo] + v[kHi]);
+            } else {
 #pragma unroll
-            for (int c = 0; c < OddEvenNet<NPAD>::kCount; ++c) {
-                const float lo = fminf(v[net.lo[c]], v[net.hi[c]]);
-                const float hi = fmaxf(v[net.lo[c]], v[net.hi[c]]);
-                v[net.lo[c]] = lo;
-                v[net.hi[c]] = hi;
+                for (int i = 0; i < NPAD; ++i) v[i] = (i < a.n_outer) ? yk(outer[i]) : INFINITY;
+#pragma unroll
+                for (int c = 0; c < OddEvenNet<NPAD>::kCount; ++c) {
+                    const float lo = fminf(v[net.lo[c]], v[net.hi[c]]);
+                    const float hi = fmaxf(v[net.lo[c]], v[net.hi[c]]);
+                    v[net.lo[c]] = lo;
+                    v[net.hi[c]] = hi;
+                }
+                const int rlo = (a.n_outer - 1) >> 1, rhi = a.n_outer >> 1;
+                float vlo = 0.f, vhi = 0.f;
+#pragma unroll
+                for (int i = 0; i < NPAD; ++i) {
+                    vlo = (i == rlo) ? v[i] : vlo;
+                    vhi = (i == rhi) ? v[i] : vhi;
+                }
+                B0 = 0.5f * (vlo + vhi);
             }
-            const int rlo = (a.n_outer - 1) >> 1, rhi = a.n_outer >> 1;
-            float vlo = 0.f, vhi = 0.f;
-#pragma unroll
-            for (int i = 0; i < NPAD; ++i) {
-                vlo = (i == rlo) ? v[i] : vlo;
-                vhi = (i == rhi) ? v[i] : vhi;
-            }
-            const float B0 = 0.5f * (vlo + vhi);
             moment_finish(yk, [&](int k) { return us[k]; }, T, B0, a.u_mid, a.du, a.span, a.x_mid, a.x_scale,
                           a.p0_out + fo * 4, a.flag_out ? a.flag_out + fo : nullptr);
         }
@@ -738,13 +750,22 @@ void* fast_readout_ptr(int Q, int sample_bytes)
     }
 }
 
-void* init_ptr(int npad)
+// the outer-set sizes of the workload geometries (21, 99, 201 and 221 teeth:
+// the outer fifth with ties kept) have their own pruned median
+void* init_ptr(int npad, int n_outer)
 {
+    switch (n_outer) {
+    case 6: return reinterpret_cast<void*>(&init_kernel<8, 6>);
+    case 20: return reinterpret_cast<void*>(&init_kernel<32, 20>);
+    case 42: return reinterpret_cast<void*>(&init_kernel<64, 42>);
+    case 46: return reinterpret_cast<void*>(&init_kernel<64, 46>);
+    default: break;
+    }
     switch (npad) {
-    case 8: return reinterpret_cast<void*>(&init_kernel<8>);
-    case 16: return reinterpret_cast<void*>(&init_kernel<16>);
-    case 32: return reinterpret_cast<void*>(&init_kernel<32>);
-    case 64: return reinterpret_cast<void*>(&init_kernel<64>);
+    case 8: return reinterpret_cast<void*>(&init_kernel<8, 0>);
+    case 16: return reinterpret_cast<void*>(&init_kernel<16, 0>);
+    case 32: return reinterpret_cast<void*>(&init_kernel<32, 0>);
+    case 64: return reinterpret_cast<void*>(&init_kernel<64, 0>);
     default: return nullptr;
     }
 }
@@ -872,7 +893,7 @@ cudaError_t launch_init(const cg_plan_s* p, const float* y, const float* amps, i
     const int64_t blocks = (tasks + 3) / 4;
     const int grid = static_cast<int>(blocks < p->grid_init ? blocks : p->grid_init);
     void* args[] = {&a};
-    return cudaLaunchKernel(init_ptr(p->init_npad), dim3(grid), dim3(128), args, p->init_smem, s);
+    return cudaLaunchKernel(init_ptr(p->init_npad, p->n_outer), dim3(grid), dim3(128), args, p->init_smem, s);
 }
 
 cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, int64_t n,

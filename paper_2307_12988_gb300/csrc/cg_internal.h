@@ -320,7 +320,7 @@ FitArgs make_fit_args(const cg_plan_s* p);
 
 // throughput path (cg_fast.cu)
 void* fast_readout_ptr(int Q, int sample_bytes = 2);
-void* init_ptr(int npad);
+void* init_ptr(int npad, int n_outer);
 int init_npad(int n_outer);
 void* fit2_ptr(int G, int PPL, bool exact, int model);
 int fit2_ppl(int G, int T, bool* exact, int model);

@@ -4,9 +4,9 @@
 // TAOCP vol. 3, 5.3.4), as a list of comparators (lo, hi): after each one,
 // wire lo holds the smaller and wire hi the larger of the two values.
 //
-// RankNet<N, NREAL, RANK>: that network reduced to what one output, the
-// RANK-th smallest (from 0) of NREAL values, needs, when wires NREAL..N-1
-// hold +infinity:
+// RankNet<N, NREAL, RANK, RANK2>: that network reduced to what the outputs
+// RANK and RANK2 (the RANK-th and RANK2-th smallest, from 0, of NREAL
+// values) need, when wires NREAL..N-1 hold +infinity:
 //   * a forward pass follows the infinite pads: a comparator with an infinite
 //     hi input changes nothing (dropped); one with an infinite lo input only
 //     moves the hi value down (a register move, kept as a move);
@@ -51,7 +51,7 @@ struct OddEvenNet {
 // step kinds of RankNet
 enum : int { kNetSkip = 0, kNetMin = 1, kNetMax = 2, kNetBoth = 3, kNetMove = 4 };
 
-template <int N, int NREAL, int RANK>
+template <int N, int NREAL, int RANK, int RANK2 = RANK>
 struct RankNet {
     static constexpr int kCount = OddEvenNet<N>::kCount;
     int lo[kCount], hi[kCount], kind[kCount];
@@ -78,6 +78,7 @@ struct RankNet {
         // backward: what the output needs
         bool need[N] = {};
         need[RANK] = true;
+        need[RANK2] = true;
         for (int c = kCount - 1; c >= 0; --c) {
             const int l = lo[c], h = hi[c];
             if (kind[c] == kNetMove) {
@@ -96,13 +97,14 @@ struct RankNet {
     }
 };
 
-// RANK-th smallest of v[0..NREAL) (v[NREAL..N) are not read); v is clobbered.
-template <int N, int NREAL, int RANK>
-__device__ __forceinline__ float rank_select(float (&v)[N])
+// Leaves the RANK-th and RANK2-th smallest of v[0..NREAL) in v[RANK] and
+// v[RANK2] (v[NREAL..N) are not read; the other entries are clobbered).
+template <int N, int NREAL, int RANK, int RANK2 = RANK>
+__device__ __forceinline__ void rank_network(float (&v)[N])
 {
-    constexpr RankNet<N, NREAL, RANK> net{};
+    constexpr RankNet<N, NREAL, RANK, RANK2> net{};
 #pragma unroll
-    for (int c = 0; c < RankNet<N, NREAL, RANK>::kCount; ++c) {
+    for (int c = 0; c < RankNet<N, NREAL, RANK, RANK2>::kCount; ++c) {
         const int l = net.lo[c], h = net.hi[c];
         if (net.kind[c] == kNetBoth) {
             const float a = v[l], b = v[h];
@@ -116,6 +118,13 @@ __device__ __forceinline__ float rank_select(float (&v)[N])
             v[l] = v[h];
         }
     }
+}
+
+// RANK-th smallest of v[0..NREAL) (v[NREAL..N) are not read); v is clobbered.
+template <int N, int NREAL, int RANK>
+__device__ __forceinline__ float rank_select(float (&v)[N])
+{
+    rank_network<N, NREAL, RANK>(v);
     return v[RANK];
 }
 
