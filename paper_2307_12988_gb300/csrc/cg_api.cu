@@ -303,9 +303,9 @@ cudaError_t setup_fit_kernels(cg_plan_s* p)
         if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
     p->G2 = G;
     p->PPL = ppl;
-    // the FP32 solve with lanes per frame left to the library: the
-    // shared-memory kernel where it is instantiated
-    if (p->opts.lanes_per_frame == 0 && !p->solve_f64 && (e = cg::setup_fit3(p)) != cudaSuccess) return e;
+    // lanes per frame left to the library: the shared-memory kernel where it
+    // is instantiated
+    if (p->opts.lanes_per_frame == 0 && (e = cg::setup_fit3(p)) != cudaSuccess) return e;
     // 0: the whole call is one chunk (one launch per kernel; measured fastest
     // for large calls, since each kernel then has frames enough for every SM)
     p->chunk = p->opts.chunk_frames ? p->opts.chunk_frames : (int64_t(1) << 40);

@@ -944,11 +944,10 @@ cudaError_t launch_fit2(const cg_plan_s* p, const float* y, const float* amps, i
     a.solve_f64 = p->solve_f64;
     a.n_rows = n;
     a.err = p->d.err;
-    // the FP32 solve takes the shared-memory kernel where one is instantiated
-    // for the tooth count and lineshape (the Lorentzian from a given guess;
-    // the Fano profile from a given centre or its lowest tooth)
-    if (p->fit3_ok && !p->solve_f64 && (p0 != nullptr || p->opts.model == CG_MODEL_FANO))
-        return launch_fit3(p, a, s);
+    // the shared-memory kernel where one is instantiated for the tooth count,
+    // lineshape and solve precision (the Lorentzian from a given guess; the
+    // Fano profile from a given centre or its lowest tooth)
+    if (p->fit3_ok && (p0 != nullptr || p->opts.model == CG_MODEL_FANO)) return launch_fit3(p, a, s);
     // tasks are claimed dynamically: a few frames per lane group per task
     const int gpw = 32 / p->G2;                   // groups per warp
     a.task = 2 * gpw;

@@ -294,7 +294,47 @@ __global__ void __launch_bounds__(256, 2) fit3_kernel(Fit2Args a)
         float pe[4] = {p[0], p[1], p[2], p[3]};
         bool done = false;
         const bool trial = f >= 0 && !fresh;
-        if (trial) {
+        if (a.solve_f64) {
+            // the normal equations solved in FP64 (the tensor-core form): FP64
+            // is scarce, so with several lanes per frame the group's leader
+            // solves and the group takes its step (shuffles outside the branch)
+            float d4[4] = {0.f, 0.f, 0.f, 0.f};
+            int okl = 0;
+            if (trial && gl == 0) {
+                if constexpr (MODEL == 1) {
+                    int held = 0;
+                    if ((p[2] <= a.fano_Alo && Nm.b[1] < 0.f) || (p[2] >= a.fano_Ahi && Nm.b[1] > 0.f)) held |= 2;
+                    if ((p[3] <= a.fano_Blo && Nm.b[2] < 0.f) || (p[3] >= a.fano_Bhi && Nm.b[2] > 0.f)) held |= 4;
+                    float d3[3] = {0.f, 0.f, 0.f};
+                    okl = lm_solve3<double>(Nm, lambda, held, d3) ? 1 : 0;
+                    d4[0] = d3[0];
+                    d4[1] = d3[1];
+                    d4[2] = d3[2];
+                } else {
+                    okl = lm_solve4_f64(Nm, lambda, d4) ? 1 : 0;
+                }
+            }
+            if constexpr (G > 1) {
+                okl = __shfl_sync(kFull, okl, leader_lane);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) d4[i] = __shfl_sync(kFull, d4[i], leader_lane);
+            }
+            if (trial) {
+                if (okl) {
+                    if constexpr (MODEL == 1) {
+                        pe[0] = p[0] + d4[0];
+                        pe[2] = fminf(fmaxf(p[2] + d4[1], a.fano_Alo), a.fano_Ahi);
+                        pe[3] = fminf(fmaxf(p[3] + d4[2], a.fano_Blo), a.fano_Bhi);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) pe[i] = p[i] + d4[i];
+                    }
+                } else {
+                    st = kSingular;
+                    done = true;
+                }
+            }
+        } else if (trial) {
             if constexpr (MODEL == 1) {
                 // a scale or offset on its bound with the gradient pointing
                 // outward is held for this step (active set); c steps freely,
@@ -549,24 +589,33 @@ size_t fit3_bytes(int warps)
 
 struct Fit3Inst {
     int G, T, model;
+    int f64;   // 1: the instance for the FP64 solve (one lane per frame where it fits)
     void* (*fn)();
     size_t (*bytes)(int);
 };
 // the workload geometries: 21 teeth (one lane per frame), 99 (two lanes),
 // 201 and 221 (four lanes)
 // (the Fano profile at the paper's 99 teeth)
+// (FP64 solve: one lane per frame at 21 and 99 teeth, so that all 32 lanes
+// of a warp solve at once; at 201 and 221 teeth the slots of one lane per
+// frame do not fit, and the group leaders solve)
 const Fit3Inst kFit3[] = {
-    {1, 21, 0, fit3_fn<1, 21, 0>, fit3_bytes<1, 21>},
-    {2, 99, 0, fit3_fn<2, 99, 0>, fit3_bytes<2, 99>},
-    {4, 201, 0, fit3_fn<4, 201, 0>, fit3_bytes<4, 201>},
-    {4, 221, 0, fit3_fn<4, 221, 0>, fit3_bytes<4, 221>},
-    {2, 99, 1, fit3_fn<2, 99, 1>, fit3_bytes<2, 99>},
+    {1, 21, 0, 0, fit3_fn<1, 21, 0>, fit3_bytes<1, 21>},
+    {2, 99, 0, 0, fit3_fn<2, 99, 0>, fit3_bytes<2, 99>},
+    {4, 201, 0, 0, fit3_fn<4, 201, 0>, fit3_bytes<4, 201>},
+    {4, 221, 0, 0, fit3_fn<4, 221, 0>, fit3_bytes<4, 221>},
+    {2, 99, 1, 0, fit3_fn<2, 99, 1>, fit3_bytes<2, 99>},
+    {1, 21, 0, 1, fit3_fn<1, 21, 0>, fit3_bytes<1, 21>},
+    {1, 99, 0, 1, fit3_fn<1, 99, 0>, fit3_bytes<1, 99>},
+    {4, 201, 0, 1, fit3_fn<4, 201, 0>, fit3_bytes<4, 201>},
+    {4, 221, 0, 1, fit3_fn<4, 221, 0>, fit3_bytes<4, 221>},
+    {1, 99, 1, 1, fit3_fn<1, 99, 1>, fit3_bytes<1, 99>},
 };
 
-const Fit3Inst* fit3_find(int T, int model)
+const Fit3Inst* fit3_find(int T, int model, int f64)
 {
     for (const Fit3Inst& f : kFit3)
-        if (f.T == T && f.model == model) return &f;
+        if (f.T == T && f.model == model && f.f64 == f64) return &f;
     return nullptr;
 }
 
@@ -578,7 +627,7 @@ const Fit3Inst* fit3_find(int T, int model)
 cudaError_t setup_fit3(cg_plan_s* p)
 {
     p->fit3_ok = false;
-    const Fit3Inst* fi = fit3_find(p->T, p->opts.model);
+    const Fit3Inst* fi = fit3_find(p->T, p->opts.model, p->solve_f64 ? 1 : 0);
     if (!fi) return cudaSuccess;
     int smem_sm = 0, smem_block = 0;
     cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
@@ -605,7 +654,7 @@ cudaError_t setup_fit3(cg_plan_s* p)
 
 cudaError_t launch_fit3(const cg_plan_s* p, Fit2Args a, cudaStream_t s)
 {
-    const Fit3Inst* fi = fit3_find(p->T, p->opts.model);
+    const Fit3Inst* fi = fit3_find(p->T, p->opts.model, p->solve_f64 ? 1 : 0);
     if (!fi || !p->fit3_ok) return cudaErrorInvalidValue;
     const int gpw = 32 / fi->G;   // groups per warp
     a.task = 2 * gpw;
