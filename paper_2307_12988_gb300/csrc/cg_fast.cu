@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(128) fast_readout_kernel(FastArgs a)
             for (int v = 0; v < P; ++v) {
                 const int k = tom[u + Q * v];
                 if (k >= 0) {
-                    const float av = sqrtf(fmaf(z[v].x, z[v].x, z[v].y * z[v].y));
+                    const float av = cabs_approx(z[v]);
                     if (a.amps) a.amps[orow + k] = av;
                     if (a.y) a.y[orow + k] = __fmul_rn(av, iref[k]);
                 }

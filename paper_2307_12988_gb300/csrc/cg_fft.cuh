@@ -76,6 +76,15 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 }
 // multiply by -i
 __device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
+// |X| by the hardware's approximate square root (one instruction, within
+// about an ulp: far inside the readout's 1e-5 of the reference), where
+// sqrtf's correctly rounded sequence took most of the last stage's time
+__device__ __forceinline__ float cabs_approx(float2 X)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(fmaf(X.x, X.x, X.y * X.y)));
+    return r;
+}
 
 // ---------------------------------------------------------------------------
 // forward DFT codelets in registers: X[v] = sum_t a[t] exp(-2 pi i v t / R)

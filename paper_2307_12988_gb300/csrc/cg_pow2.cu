@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kPow2Threads) pow2_readout_kernel(ReadoutArgs 
             const float2 Dd = make_float2(0.5f * (Zb.x - Zr.x), 0.5f * (Zb.y + Zr.y));
             const float2 O = make_float2(Dd.y, -Dd.x);
             const float2 X = cadd(E, cmul(twb[k], O));
-            const float amp = sqrtf(fmaf(X.x, X.x, X.y * X.y));
+            const float amp = cabs_approx(X);
             const int64_t o = (f0 + f) * T + k;
             if (a.amps) a.amps[o] = amp;
             if (a.y) a.y[o] = __fmul_rn(amp, iref[k]);
