@@ -73,8 +73,10 @@ __global__ void __launch_bounds__(192, 1) dft_gemm_kernel(const __grid_constant_
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t m0 = static_cast<int64_t>(blockIdx.x) * kBM;
-    const int nt = blockIdx.y;
+    // consecutive blocks are the column tiles of one frame tile: they run
+    // together, so the frame tile's samples come from DRAM once
+    const int64_t m0 = static_cast<int64_t>(blockIdx.x / a.n_ctiles) * kBM;
+    const int nt = static_cast<int>(blockIdx.x % a.n_ctiles);
     const int nkb = a.nkb;
 
     if (threadIdx.x == 0) {
@@ -349,8 +351,10 @@ __global__ void __launch_bounds__((4 * HALVES + 2) * 32, 1) dft_gemm_ring_kernel
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t m0 = static_cast<int64_t>(blockIdx.x) * (HALVES * kBM);
-    const int nt = blockIdx.y;
+    // consecutive blocks are the column tiles of one frame tile: they run
+    // together, so the frame tile's samples come from DRAM once
+    const int64_t m0 = static_cast<int64_t>(blockIdx.x / a.n_ctiles) * (HALVES * kBM);
+    const int nt = static_cast<int>(blockIdx.x % a.n_ctiles);
     const int nkb = a.nkb;
     constexpr int kTmaWarp = 4 * HALVES, kMmaWarp = 4 * HALVES + 1;
 
@@ -594,6 +598,7 @@ cudaError_t setup_gemm(cg_plan_s* p)
     g.T = T;
     g.nkb = nkb;
     g.ntile = NT;
+    g.n_ctiles = ntiles;
     g.nrows_total = rows_total;
     // FP32 accumulation error grows with the coherent partial sum; alternate
     // the K blocks over as many accumulators as fit in the 512 TMEM columns
@@ -650,13 +655,13 @@ cudaError_t launch_gemm_readout(const cg_plan_s* p, const int16_t* frames, int64
     if (p->gemm_ring && g.vec8) {
         const int H = p->gemm_halves;
         g.stages = p->gemm_ring_stages;
-        dim3 grid2(static_cast<unsigned>((n + H * kBM - 1) / (H * kBM)), static_cast<unsigned>(p->gemm_ntiles));
+        dim3 grid2(static_cast<unsigned>((n + H * kBM - 1) / (H * kBM) * p->gemm_ntiles));
         void* args2[] = {const_cast<CUtensorMap*>(&p->gemm_map), &g};
         void* rk = H == 2 ? reinterpret_cast<void*>(&dft_gemm_ring_kernel<2>)
                           : reinterpret_cast<void*>(&dft_gemm_ring_kernel<1>);
         return cudaLaunchKernel(rk, grid2, dim3((4 * H + 2) * 32), args2, p->gemm_ring_smem, s);
     }
-    dim3 grid(static_cast<unsigned>((n + kBM - 1) / kBM), static_cast<unsigned>(p->gemm_ntiles));
+    dim3 grid(static_cast<unsigned>((n + kBM - 1) / kBM * p->gemm_ntiles));
     void* fn = p->gemm_split_x ? reinterpret_cast<void*>(&dft_gemm_kernel<true>)
                                : reinterpret_cast<void*>(&dft_gemm_kernel<false>);
     void* args[] = {const_cast<CUtensorMap*>(&p->gemm_map), &g};

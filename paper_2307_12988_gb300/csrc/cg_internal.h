@@ -144,6 +144,7 @@ struct GemmArgs {
     int N, T;
     int nkb;                 // K blocks of 64 samples
     int ntile;               // output columns per tile (2 per tooth), multiple of 16
+    int n_ctiles;            // column tiles (block b: frame tile b / n_ctiles, column tile b % n_ctiles)
     int nrows_total;         // rows of one (hi or lo) half of the twiddle matrix
     int tmem_cols;           // TMEM columns allocated per block (n_acc * acc_cols)
     int acc_cols;            // columns of one accumulator
