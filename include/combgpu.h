@@ -361,7 +361,10 @@ cg_status cg_mlp_create(cg_mlp_t* mlp, int n_in, int n_hidden, int n_out, int ma
 void cg_mlp_destroy(cg_mlp_t mlp);
 
 /* Copy the parameters to / from host float [count]; count must equal
- * cg_mlp_param_count.  set_params also clears the Adam state. Synchronous. */
+ * cg_mlp_param_count.  set_params also clears the Adam state. Synchronous.
+ * get_params (and cg_mlp_save) return CG_ERR_TIMEOUT when a matrix-product
+ * block of an earlier asynchronous call gave up a bounded wait (its outputs,
+ * and everything computed from them, are then invalid); the flag is cleared. */
 cg_status cg_mlp_get_params(cg_mlp_t mlp, float* params_host, int64_t count);
 cg_status cg_mlp_set_params(cg_mlp_t mlp, const float* params_host, int64_t count);
 
