@@ -723,6 +723,89 @@ def run_psd(args):
     print(json.dumps(line), flush=True)
 
 
+def run_train(args):
+    """The learned-guess training leg: epochs of ``cg_mlp_train_epoch`` (gather,
+    forward, MSE, backward, Adam on the device) over --train-rows standardised
+    spectra of --train-in teeth, hidden width --train-hidden, minibatches of
+    --train-batch; a step is one epoch.  Throughput does not depend on the
+    values, so rows and targets are seeded normal draws."""
+    import torch
+    import paper_2307_12988_gb300 as cg
+    from oracle import mlp as omlp
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n, ni, H, no, B = args.train_rows, args.train_in, args.train_hidden, 4, args.train_batch
+    g = torch.Generator(device="cpu").manual_seed(5)
+    xh = torch.randn(n, ni, generator=g)
+    th = torch.randn(n, no, generator=g)
+    perm_h = torch.randperm(n, generator=g).to(torch.int32)
+    x, t, perm = xh.to(dev), th.to(dev), perm_h.to(dev)
+    net = cg.Mlp(ni, H, no, max_batch=B, seed=1)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        net.train_epoch(x, t, perm, B, 1e-4)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        losses = net.train_epoch(x, t, perm, B, 1e-4)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    net.params()   # raises if a product block gave up a bounded wait
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    value = n / (ms / 1e3)
+    per_row = 2.0 * (ni * H + H * H + H * no)          # forward multiply-adds x 2
+    flops = 3.0 * per_row * n                           # forward + the two backward products
+    hbm, bf16, peak_kind = _peaks()
+    tf32_peak = bf16 * (1.1 / 2.25)                     # nominal TF32 : BF16 dense ratio
+    achieved = 3.0 * flops / (ms / 1e3) / 1e12          # three TF32 products per FP32 product
+    # end to end: the epoch's rows and targets from pinned host memory, the
+    # losses back
+    xp, tp = xh.pin_memory(), th.pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.e2e_steps)):
+        xd, td = xp.to(dev, non_blocking=True), tp.to(dev, non_blocking=True)
+        lo = net.train_epoch(xd, td, perm, B, 1e-4)
+        lo.cpu()
+    e2e_s = (time.perf_counter() - t0) / max(1, args.e2e_steps)
+    # the oracle (FP64 NumPy) on a bounded sample: whole minibatch gradients
+    theta = net.params().astype(np.float64)
+    xb, tb = xh[:B].numpy().astype(np.float64), th[:B].numpy().astype(np.float64)
+    t0, rows_cpu = time.perf_counter(), 0
+    while time.perf_counter() - t0 < min(args.cpu_seconds, 10.0):
+        omlp.loss_and_grad(theta, xb, tb, ni, H, no)
+        rows_cpu += B
+    cpu_s = time.perf_counter() - t0
+    line = {
+        "metric": "learned-guess training rows/s (forward, MSE, backward, Adam)",
+        "value": value, "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (products as three TF32 tensor-core products)", "data": "synthetic",
+        "config": {"workload": f"mlp_train_{ni}x{H}x{H}x{no}_batch{B}", "rows": n,
+                   "l2": "epoch inputs resident; no flush (each minibatch is read once per epoch)"},
+        "final_batch_loss": float(losses[-1].item()),
+        "roofline": {"kernel": "tgemm_kernel", "bound": "tensor", "achieved": achieved, "peak": tf32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / tf32_peak, "traffic": None,
+                     "peak_kind": f"{peak_kind} bf16 x nominal tf32/bf16 ratio",
+                     "note": "whole epoch time, small kernels included; three TF32 products counted"},
+        "e2e": {"value": n / e2e_s, "unit": "rows/s", "h2d_bytes_per_step": 4 * n * (ni + no),
+                "d2h_bytes_per_step": 4 * ((n + B - 1) // B)},
+        "cpu_baseline": {"value": rows_cpu / cpu_s, "unit": "rows/s",
+                         "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+                         "kind": "oracle", "sample": f"{rows_cpu} rows: FP64 NumPy minibatch gradients, no Adam"},
+        "clocks": clk,
+        # per minibatch: 2 gathers, 8 products, MSE + loss, 3 column sums,
+        # Adam (+ one sum per K-split product, not counted)
+        "gpu_launches": 16 * ((n + B - 1) // B) * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -760,11 +843,18 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=32768, help="pre-generated frames replayed per stream")
     ap.add_argument("--serve-budget", type=int, default=4 << 30)
     ap.add_argument("--psd-only", action="store_true", help="run only the displacement-PSD leg")
+    ap.add_argument("--train-only", action="store_true", help="run only the learned-guess training leg")
+    ap.add_argument("--train-rows", type=int, default=200_000)
+    ap.add_argument("--train-in", type=int, default=221)
+    ap.add_argument("--train-hidden", type=int, default=256)
+    ap.add_argument("--train-batch", type=int, default=1024)
     ap.add_argument("--psd-seconds", type=float, default=600.0, help="series length (the paper's longest PSD: 10 min)")
     ap.add_argument("--psd-seg", type=int, default=32768, help="Welch segment length")
     args = ap.parse_args()
     if args.psd_only:
         run_psd(args)
+    elif args.train_only:
+        run_train(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.serve_only:
