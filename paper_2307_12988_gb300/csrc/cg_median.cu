@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
     const int W = T + 6;                                               // padded columns
     float* tile = reinterpret_cast<float*>(msm);                       // [R + 6][S], column j = tooth j - 3
     float* cm = tile + (R + 6) * S;                                    // [R][S]
-    int* list = reinterpret_cast<int*>(cm + R * S);                    // [R T]
+    uint16_t* list = reinterpret_cast<uint16_t*>(cm + R * S);          // [R T]: (row << 9) | tooth
     unsigned long long* key = reinterpret_cast<unsigned long long*>(msm + a.sm_key);   // [R]
     int* count = reinterpret_cast<int*>(key + R);
     int* ka = count + 4;                                               // [R] first window of least U
@@ -209,7 +209,11 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
         if (tid == 0) *count = 0;
         __syncthreads();
         // 2. medians of the 7-row column segments: one thread per column and
-        //    16 consecutive rows loads the column's 22 values once
+        //    16 consecutive rows loads the column's 22 values once.  Two
+        //    adjacent segments share 6 values: with s2 <= s3 their 3rd and 4th
+        //    smallest, the median of the 6 and one more value x is
+        //    min(max(x, s2), s3), so a pair costs one pruned 6-input selection
+        //    and 4 operations
         for (int idx = tid; idx < W * ((rows + 15) / 16); idx += kMedThreads) {
             const int h = idx / W;
             const int j = idx - h * W;
@@ -219,8 +223,15 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
 #pragma unroll
             for (int q = 0; q < 22; ++q) col[q] = q < nr + 6 ? tile[(r0 + q) * S + j] : 0.f;
 #pragma unroll
-            for (int rr = 0; rr < 16; ++rr) {
-                if (rr < nr) {
+            for (int rr = 0; rr < 16; rr += 2) {
+                if (rr + 1 < nr) {
+                    float v[8];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) v[q] = col[rr + 1 + q];
+                    rank_network<8, 6, 2, 3>(v);
+                    cm[(r0 + rr) * S + j] = fminf(fmaxf(col[rr], v[2]), v[3]);
+                    cm[(r0 + rr + 1) * S + j] = fminf(fmaxf(col[rr + 7], v[2]), v[3]);
+                } else if (rr < nr) {
                     float v[7];
 #pragma unroll
                     for (int q = 0; q < 7; ++q) v[q] = col[rr + q];
@@ -229,23 +240,42 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
             }
         }
         __syncthreads();
-        // 3. per row (one warp): bounds and the candidate windows
+        // 3. per row (one warp): bounds and the candidate windows.  Lane l
+        //    takes the KPL consecutive windows k0 = KPL l .. k0 + KPL - 1,
+        //    which span the KPL + 6 column medians c[k0 ..].  In blocks of 7
+        //    (van Herk / Gil-Werman), window q is the whole block when q is a
+        //    multiple of 7, else a suffix of one block and a prefix of the
+        //    next: two running extremes per value and one more per window
         for (int r = warp; r < rows; r += kWarps) {
             const float* cr = cm + r * S;
+            const int k0 = KPL * lane;
+            constexpr int kC = KPL + 6;
+            float c[kC];
+#pragma unroll
+            for (int q = 0; q < kC; ++q) c[q] = k0 + q < W ? cr[k0 + q] : 0.f;
+            float smin[kC], smax[kC], pmin[kC], pmax[kC];   // suffix / prefix extremes within blocks of 7
+#pragma unroll
+            for (int q = kC - 1; q >= 0; --q) {
+                const bool last = q % 7 == 6 || q == kC - 1;
+                smin[q] = last ? c[q] : fminf(c[q], smin[last ? q : q + 1]);
+                smax[q] = last ? c[q] : fmaxf(c[q], smax[last ? q : q + 1]);
+            }
+#pragma unroll
+            for (int q = 0; q < kC; ++q) {
+                const bool first = q % 7 == 0;
+                pmin[q] = first ? c[q] : fminf(pmin[first ? q : q - 1], c[q]);
+                pmax[q] = first ? c[q] : fmaxf(pmax[first ? q : q - 1], c[q]);
+            }
+            float lo[KPL];                         // L(k) of this lane's windows
             float ustar = INFINITY;
             int kbest = 0x7fffffff;
-            float lo[KPL];                         // L(k) of this lane's windows
 #pragma unroll
             for (int q = 0; q < KPL; ++q) {
-                const int k = lane + 32 * q;
+                const float l = q % 7 == 0 ? smin[q] : fminf(smin[q], pmin[q + 6]);
+                const float hi = q % 7 == 0 ? smax[q] : fmaxf(smax[q], pmax[q + 6]);
+                const int k = k0 + q;
                 lo[q] = INFINITY;
                 if (k < T) {
-                    float l = cr[k], hi = cr[k];
-#pragma unroll
-                    for (int d = 1; d < 7; ++d) {
-                        l = fminf(l, cr[k + d]);
-                        hi = fmaxf(hi, cr[k + d]);
-                    }
                     lo[q] = l;
                     if (hi < ustar) {
                         ustar = hi;
@@ -263,17 +293,26 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
                 }
             }
             if (lane == 0) ka[r] = kbest < T ? kbest : 0;
+            int mine = 0;                          // this lane's candidates
+            bool cand[KPL];
 #pragma unroll
             for (int q = 0; q < KPL; ++q) {
-                const int k = lane + 32 * q;
-                if (32 * q >= T) break;
-                const bool cand = k < T && !(lo[q] > ustar);   // (non-finite rows keep every window)
-                const unsigned bal = __ballot_sync(0xffffffffu, cand);
-                int base = 0;
-                if (lane == 0 && bal) base = atomicAdd(count, __popc(bal));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (cand) list[base + __popc(bal & ((1u << lane) - 1u))] = (r << 16) | k;
+                cand[q] = k0 + q < T && !(lo[q] > ustar);   // (non-finite rows keep every window)
+                mine += cand[q] ? 1 : 0;
             }
+            int incl = mine;                       // inclusive prefix sum over lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            int base = 0;
+            if (lane == 0 && total > 0) base = atomicAdd(count, total);
+            base = __shfl_sync(0xffffffffu, base, 0) + incl - mine;
+#pragma unroll
+            for (int q = 0; q < KPL; ++q)
+                if (cand[q]) list[base++] = static_cast<uint16_t>((r << 9) | (k0 + q));
         }
         __syncthreads();
         // 4. the exact median t of each row's window of least U (an upper
@@ -288,8 +327,14 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
         const int nc = *count;
         for (int e = tid; e < nc; e += kMedThreads) {
             const int it = list[e];
-            const int r = it >> 16, k = it & 0xffff;
+            const int r = it >> 9, k = it & 0x1ff;
             const float t = tq[r];
+            // L(k) > t: the window's median exceeds t (no count needed)
+            const float* cr = cm + r * S + k;
+            float l = cr[0];
+#pragma unroll
+            for (int d = 1; d < 7; ++d) l = fminf(l, cr[d]);
+            if (l > t) continue;
             int lt = 0, le = 0;
 #pragma unroll
             for (int c = 0; c < 7; ++c)
@@ -342,7 +387,7 @@ cudaError_t setup_median(cg_plan_s* p)
     int R = 32;
     auto bytes = [&](int r) {
         const size_t tables = sizeof(float) * (static_cast<size_t>(r + 6) * S + static_cast<size_t>(r) * S) +
-                              sizeof(int) * static_cast<size_t>(r) * T;
+                              sizeof(uint16_t) * static_cast<size_t>(r) * T;
         const size_t rest = ((tables + 15) & ~static_cast<size_t>(15)) + 8 * r + 16 + 12 * r + 4 * (T + 6) + 4 * T;
         const size_t raw = sizeof(float) * ((static_cast<size_t>(r + 6) * T + 4 + 3) & ~static_cast<size_t>(3));
         return ((rest + 15) & ~static_cast<size_t>(15)) + raw;
@@ -350,7 +395,7 @@ cudaError_t setup_median(cg_plan_s* p)
     while (R > 4 && bytes(R) > 100 * 1024) R /= 2;
     m.R = R;
     const size_t tables = sizeof(float) * (static_cast<size_t>(R + 6) * S + static_cast<size_t>(R) * S) +
-                          sizeof(int) * static_cast<size_t>(R) * T;
+                          sizeof(uint16_t) * static_cast<size_t>(R) * T;
     m.sm_key = static_cast<int>((tables + 15) & ~static_cast<size_t>(15));
     {
         const size_t rest = static_cast<size_t>(m.sm_key) + 8 * R + 16 + 12 * R + 4 * (T + 6) + 4 * T;
