@@ -43,7 +43,7 @@ namespace cg {
 namespace {
 
 constexpr int kMedThreads = 256;
-constexpr int kMaxKPerLane = 16;   // windows per lane in the bounds pass: T <= 512
+constexpr int kMaxTeeth = 512;     // 16 windows on each of 32 lanes in the bounds pass
 
 __device__ __forceinline__ void cmpx(float& a, float& b)
 {
@@ -134,10 +134,9 @@ __device__ __forceinline__ float window_median(const float* tile, int S, int r, 
     return rank_select<32, 29, 14>(v);
 }
 
-// KPL: windows per lane in the bounds pass (T <= 32 KPL), a compile-time
-// count so that no unrolled step runs past the row
-template <int KPL>
-__global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
+// LPR: lanes per row in the bounds pass, 16 windows each (T <= 16 LPR)
+template <int LPR>
+__global__ void __launch_bounds__(kMedThreads, 4) median_init_kernel(MedianArgs a)
 {
     extern __shared__ __align__(16) unsigned char msm[];
     const int R = a.R, T = a.T, S = a.S;
@@ -158,6 +157,7 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kMedThreads / 32;
+    constexpr int kRPW = 32 / LPR;                                     // rows per warp in the bounds pass
     for (int j = tid; j < W; j += kMedThreads) mir[j] = mirror(j - 3, T);
     for (int k = tid; k < T; k += kMedThreads) iref[k] = a.y ? 1.0f : a.inv_ref[k];
     // the rows a block needs, [rlo, rhi): its own and 3 on either side, within
@@ -240,51 +240,38 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
             }
         }
         __syncthreads();
-        // 3. per row (one warp): bounds and the candidate windows.  Lane l
-        //    takes the KPL consecutive windows k0 = KPL l .. k0 + KPL - 1,
-        //    which span the KPL + 6 column medians c[k0 ..].  In blocks of 7
-        //    (van Herk / Gil-Werman), window q is the whole block when q is a
-        //    multiple of 7, else a suffix of one block and a prefix of the
-        //    next: two running extremes per value and one more per window
-        for (int r = warp; r < rows; r += kWarps) {
-            const float* cr = cm + r * S;
-            const int k0 = KPL * lane;
-            constexpr int kC = KPL + 6;
-            float c[kC];
+        // 3. bounds and the candidate windows: LPR lanes per row, lane part p
+        //    takes the 16 consecutive windows k0 = 16 p .. k0 + 15, which span
+        //    the column medians c[k0 .. k0 + 21]; windows in fours share
+        //    their middle four values (and pairs of the others), 3.25 min or
+        //    max operations a window.  Pass 1: U and the row's least U (first
+        //    window on ties, reduced over the row's lanes); pass 2: L and the
+        //    windows with L <= U*
+        for (int rg = warp * kRPW; rg < rows; rg += kWarps * kRPW) {   // (uniform over the warp)
+            const int r = rg + lane / LPR;
+            const int k0 = 16 * (lane % LPR);
+            const bool rv = r < rows;
+            const float* cr = cm + (rv ? r : 0) * S;
+            float c[22];
 #pragma unroll
-            for (int q = 0; q < kC; ++q) c[q] = k0 + q < W ? cr[k0 + q] : 0.f;
-            float smin[kC], smax[kC], pmin[kC], pmax[kC];   // suffix / prefix extremes within blocks of 7
-#pragma unroll
-            for (int q = kC - 1; q >= 0; --q) {
-                const bool last = q % 7 == 6 || q == kC - 1;
-                smin[q] = last ? c[q] : fminf(c[q], smin[last ? q : q + 1]);
-                smax[q] = last ? c[q] : fmaxf(c[q], smax[last ? q : q + 1]);
-            }
-#pragma unroll
-            for (int q = 0; q < kC; ++q) {
-                const bool first = q % 7 == 0;
-                pmin[q] = first ? c[q] : fminf(pmin[first ? q : q - 1], c[q]);
-                pmax[q] = first ? c[q] : fmaxf(pmax[first ? q : q - 1], c[q]);
-            }
-            float lo[KPL];                         // L(k) of this lane's windows
+            for (int q = 0; q < 22; ++q) c[q] = (rv && k0 + q < W) ? cr[k0 + q] : 0.f;
             float ustar = INFINITY;
             int kbest = 0x7fffffff;
 #pragma unroll
-            for (int q = 0; q < KPL; ++q) {
-                const float l = q % 7 == 0 ? smin[q] : fminf(smin[q], pmin[q + 6]);
-                const float hi = q % 7 == 0 ? smax[q] : fmaxf(smax[q], pmax[q + 6]);
-                const int k = k0 + q;
-                lo[q] = INFINITY;
-                if (k < T) {
-                    lo[q] = l;
-                    if (hi < ustar) {
-                        ustar = hi;
-                        kbest = k;
+            for (int g = 0; g < 16; g += 4) {
+                const float m4 = fmaxf(fmaxf(c[g + 3], c[g + 4]), fmaxf(c[g + 5], c[g + 6]));
+                const float p12 = fmaxf(c[g + 1], c[g + 2]), p78 = fmaxf(c[g + 7], c[g + 8]);
+                const float u4[4] = {fmaxf(m4, fmaxf(c[g], p12)), fmaxf(m4, fmaxf(p12, c[g + 7])),
+                                     fmaxf(m4, fmaxf(c[g + 2], p78)), fmaxf(m4, fmaxf(p78, c[g + 9]))};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (rv && k0 + g + j < T && u4[j] < ustar) {
+                        ustar = u4[j];
+                        kbest = k0 + g + j;
                     }
-                }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int o = LPR / 2; o > 0; o >>= 1) {
                 const float uo = __shfl_xor_sync(0xffffffffu, ustar, o);
                 const int ko = __shfl_xor_sync(0xffffffffu, kbest, o);
                 if (uo < ustar || (uo == ustar && ko < kbest)) {
@@ -292,15 +279,20 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
                     kbest = ko;
                 }
             }
-            if (lane == 0) ka[r] = kbest < T ? kbest : 0;
-            int mine = 0;                          // this lane's candidates
-            bool cand[KPL];
+            if (rv && k0 == 0) ka[r] = kbest < T ? kbest : 0;
+            unsigned cand = 0;                     // bit q: window k0 + q
 #pragma unroll
-            for (int q = 0; q < KPL; ++q) {
-                cand[q] = k0 + q < T && !(lo[q] > ustar);   // (non-finite rows keep every window)
-                mine += cand[q] ? 1 : 0;
+            for (int g = 0; g < 16; g += 4) {
+                const float m4 = fminf(fminf(c[g + 3], c[g + 4]), fminf(c[g + 5], c[g + 6]));
+                const float p12 = fminf(c[g + 1], c[g + 2]), p78 = fminf(c[g + 7], c[g + 8]);
+                const float l4[4] = {fminf(m4, fminf(c[g], p12)), fminf(m4, fminf(p12, c[g + 7])),
+                                     fminf(m4, fminf(c[g + 2], p78)), fminf(m4, fminf(p78, c[g + 9]))};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)   // (non-finite rows keep every window)
+                    if (rv && k0 + g + j < T && !(l4[j] > ustar)) cand |= 1u << (g + j);
             }
-            int incl = mine;                       // inclusive prefix sum over lanes
+            const int mine = __popc(cand);
+            int incl = mine;                       // inclusive prefix sum over the warp
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int v = __shfl_up_sync(0xffffffffu, incl, o);
@@ -310,9 +302,11 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
             int base = 0;
             if (lane == 0 && total > 0) base = atomicAdd(count, total);
             base = __shfl_sync(0xffffffffu, base, 0) + incl - mine;
-#pragma unroll
-            for (int q = 0; q < KPL; ++q)
-                if (cand[q]) list[base++] = static_cast<uint16_t>((r << 9) | (k0 + q));
+            while (cand) {
+                const int q = __ffs(cand) - 1;
+                cand &= cand - 1;
+                list[base++] = static_cast<uint16_t>((r << 9) | (k0 + q));
+            }
         }
         __syncthreads();
         // 4. the exact median t of each row's window of least U (an upper
@@ -367,9 +361,9 @@ __global__ void __launch_bounds__(kMedThreads) median_init_kernel(MedianArgs a)
 
 static void* median_fn(int T)
 {
-    if (T <= 128) return reinterpret_cast<void*>(&median_init_kernel<4>);
-    if (T <= 256) return reinterpret_cast<void*>(&median_init_kernel<8>);
-    return reinterpret_cast<void*>(&median_init_kernel<kMaxKPerLane>);
+    if (T <= 128) return reinterpret_cast<void*>(&median_init_kernel<8>);
+    if (T <= 256) return reinterpret_cast<void*>(&median_init_kernel<16>);
+    return reinterpret_cast<void*>(&median_init_kernel<32>);
 }
 
 // Rows per block (32, 16, 8 or 4: the most whose tables fit in 100 KB of
@@ -378,7 +372,7 @@ cudaError_t setup_median(cg_plan_s* p)
 {
     p->median_ok = false;
     const int T = p->T;
-    if (T > 32 * kMaxKPerLane) return cudaSuccess;
+    if (T > kMaxTeeth) return cudaSuccess;
     const int S = (T + 6) | 1;
     MedianArgs& m = p->med;
     m = MedianArgs{};
