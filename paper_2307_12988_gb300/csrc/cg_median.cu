@@ -329,19 +329,23 @@ __global__ void __launch_bounds__(kMedThreads, 4) median_init_kernel(MedianArgs 
 #pragma unroll
             for (int d = 1; d < 7; ++d) l = fminf(l, cr[d]);
             if (l > t) continue;
-            int lt = 0, le = 0;
+            // at or below t first: fewer than 25 means a median above t,
+            // the usual case; only the others count the values below t
+            int le = 0;
 #pragma unroll
             for (int c = 0; c < 7; ++c)
 #pragma unroll
-                for (int j = 0; j < 7; ++j) {
-                    const float v = tile[(r + j) * S + k + c];
-                    lt += v < t ? 1 : 0;
-                    le += v <= t ? 1 : 0;
-                }
+                for (int j = 0; j < 7; ++j) le += tile[(r + j) * S + k + c] <= t ? 1 : 0;
+            if (le < 25) continue;
+            int lt = 0;
+#pragma unroll
+            for (int c = 0; c < 7; ++c)
+#pragma unroll
+                for (int j = 0; j < 7; ++j) lt += tile[(r + j) * S + k + c] < t ? 1 : 0;
             if (lt >= 25) {
                 const float med = window_median(tile, S, r, k);
                 atomicMin(&key[r], (static_cast<unsigned long long>(ord(med)) << 32) | static_cast<unsigned>(k));
-            } else if (le >= 25) {
+            } else {
                 atomicMin(&tie[r], k);
             }
         }
