@@ -1,8 +1,10 @@
 """Learned initial guess on the GPU against the FP64 network reference (GPU).
 
-Training kernels (FP32): forward, loss, every gradient block and one Adam
-step are compared with oracle/mlp.py on the same parameters and data;
-training is deterministic and lowers the loss.  Inference kernel (tcgen05,
+Training kernels (FP32 values; the matrix products on the tensor cores with
+each operand split into two TF32 parts): forward, loss, every gradient block
+and one Adam step are compared with oracle/mlp.py on the same parameters and
+data, at sizes that exercise one-row batches, ragged tiles and the K-split
+weight gradients; training is deterministic and lowers the loss.  Inference kernel (tcgen05,
 BF16 operands, FP32 accumulation): compared with the reference evaluated on
 the same BF16-rounded operands (input, W1, the first hidden layer, W2), so
 the remaining difference is accumulation order and the hardware exponential;
@@ -37,7 +39,8 @@ def _blocks(n_in, H, n_out):
     return [(names[i], offs[i], offs[i + 1]) for i in range(6)]
 
 
-@pytest.mark.parametrize("shape,n", [((221, 256, 4), 300), ((21, 64, 4), 77), ((99, 256, 4), 4096)])
+@pytest.mark.parametrize("shape,n", [((221, 256, 4), 300), ((21, 64, 4), 77), ((99, 256, 4), 4096),
+                                     ((37, 80, 3), 1), ((37, 80, 3), 333), ((50, 1024, 16), 1500)])
 def test_forward_loss_gradient_match_oracle(shape, n):
     n_in, H, n_out = shape
     net = cg.Mlp(n_in, H, n_out, max_batch=4096, seed=7)
