@@ -68,8 +68,10 @@ struct RootTable {
 // ---------------------------------------------------------------------------
 // complex helpers (float2 = re, im)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// (packed FP32x2 arithmetic: one instruction for both parts, each rounded as
+// the scalar operation; a - b as fma(b, -1, a), rounded once like a - b)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -167,10 +169,8 @@ struct DftOdd {
             for (int t = 1; t <= H; ++t) {
                 const float c = tab.c[(v * t) % R];
                 const float sn = tab.s[(v * t) % R];
-                P.x = fmaf(s[t].x, c, P.x);
-                P.y = fmaf(s[t].y, c, P.y);
-                Q.x = fmaf(d[t].x, sn, Q.x);
-                Q.y = fmaf(d[t].y, sn, Q.y);
+                P = __ffma2_rn(s[t], make_float2(c, c), P);
+                Q = __ffma2_rn(d[t], make_float2(sn, sn), Q);
             }
             out[v] = make_float2(P.x + Q.y, P.y - Q.x);
             out[R - v] = make_float2(P.x - Q.y, P.y + Q.x);
