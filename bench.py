@@ -213,7 +213,7 @@ MLP_BLOB = os.path.join(ROOT, "paper_2307_12988_gb300", "data", "mlp_wide_t221.c
 # DRAM bytes per frame (dram__bytes_read.sum + dram__bytes_write.sum) of one
 # ncu capture of each kernel on the paper-rate workload, by the stage names
 # of the per-kernel timing; a kernel changed since its capture has none
-NCU_TRAFFIC_PER_FRAME = {("paper_rate", "fft", "moment"): {"readout": 2519.5, "init": 407.8, "fit": 426.4}}
+NCU_TRAFFIC_PER_FRAME = {("paper_rate", "fft", "moment"): {"readout": 2523.8, "init": 397.1, "fit": 414.4}}
 
 # FP32 operations of one LM point evaluation (model, residual, Jacobian and
 # the 14 running sums of J^T J, J^T r and chi^2): 11 + 10 FMA x 2 + 4 adds
