@@ -7,7 +7,9 @@ paper's cavity is about 8): synthetic 12-bit frames are read
 out and fit by ``cg_process`` and compared frame by frame with the oracle's
 readout (|dy| <= 1e-5) and fits (every frame's status as the oracle's run
 with the same iteration cap, converged centres within 1e-4 of the dip's
-FWHM of the oracle's converged optimum).  Both sides run up to 100 LM
+FWHM of the oracle's converged optimum, or chi^2 within the LM tolerance
+of the optimum's where chi^2 is too flat for the stopping rule to place the
+centre that closely).  Both sides run up to 100 LM
 steps: on irregular tooth sets with the dip off centre the moment guess can
 start a linewidth away, and at the paper's cap of 20 the cap rather than
 the arithmetic would decide many frames' status.  The geometries exercise the general
@@ -83,5 +85,5 @@ def test_random_geometry_parity(seed):
     # (a frame neither side fits within the cap may end as max_iter on one
     # and singular on the other: both are failures, compared as one class)
     ok = W.judge_fit(got["params"], got["status"], o, conv, 1e-4 * 2 * g, f"seed {seed} N {N} T {bins.size}",
-                     failures_alike=True)
+                     failures_alike=True, y=o["y"], x=x)
     assert ok.mean() >= 0.99
