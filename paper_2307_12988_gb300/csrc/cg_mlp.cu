@@ -70,19 +70,19 @@ __device__ __forceinline__ float gelu_grad_f(float z)
 // rounding, where one TF32 product would lose 2^-11 (the three-product TF32
 // split is a standard way to recover FP32 accuracy from TF32 units).
 //
-// One block per 128 x bn output tile (bn = 16 .. 128) and K range.  Eight worker
-// warps copy 32-element K blocks of both operands straight into the K-major
-// 128-byte-swizzled tile with 4-byte cp.async (any layout, any alignment;
-// out-of-range elements zero-filled), two blocks ahead of the one they split
-// in place (hi rounded where it lies, lo beside it) for the MMAs; three
-// buffers, and the MMAs of one block run while the next is split.  Warp 8
-// owns TMEM and issues the MMAs from one lane; the workers then read the
-// accumulator out through shared memory and apply the epilogue row by row.
-// With gridDim.z > 1 block
-// z takes the z-th K range and writes its raw sum to ws[z][M][N]; a second
-// kernel adds the ranges in order of z.  Every sum has a fixed order, so
-// training stays deterministic.  Waits are bounded; on a time-out the block
-// sets the object's error word and writes nothing.
+// One block per 128 x bn output tile (bn = 16 .. 128) and K range.  Eight
+// worker warps copy 32-element K blocks of both operands straight into the
+// K-major 128-byte-swizzled tile with 4-byte cp.async (any layout, any
+// alignment; out-of-range elements zero-filled), two blocks ahead of the one
+// they split in place (hi rounded where it lies, lo beside it) for the MMAs;
+// three buffers, and the MMAs of one block run while the next is split.
+// Warp 8 owns TMEM and issues the MMAs from one lane; the workers then read
+// the accumulator out through shared memory and apply the epilogue row by
+// row.  With gridDim.z > 1, block z takes the z-th K range and writes its
+// raw sum to ws[z][M][N]; a second kernel adds the ranges in order of z.
+// Every sum has a fixed order, so training stays deterministic.  Waits are
+// bounded; on a time-out the block sets the object's error word and writes
+// nothing.
 // Epilogue: kEpiBias C = acc + bias[n]; kEpiBiasGelu C = z = acc + bias[n],
 // C2 = gelu(z); kEpiGeluGrad C = acc * gelu'(aux[m][n]).
 // ---------------------------------------------------------------------------
